@@ -1,0 +1,396 @@
+"""Pins of the FP64 CPU oracle against facts the paper and mathematics fix.
+
+Nothing here runs GPU code.  Each pin is chosen so that a plausible mistake in
+the oracle (a dropped term, a wrong sign, an index off by one, a wrong power)
+fails at least one of them; ``test_mutants_are_caught`` compiles deliberately
+broken copies of the oracle and checks exactly that.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+mpmath = pytest.importorskip("mpmath")
+
+ALPHAS = [0.3, 0.5, 0.85, 0.9, 0.98, 1.0]
+
+
+# ---------------------------------------------------------------------------
+# Weights (Sec. 2): brute-force quadrature of the product-integration kernels.
+# Product rectangle (predictor, eq. 2): f replaced by f_k on [t_k, t_{k+1}),
+#   b_{n-k} = 1/Gamma(a) * int_k^{k+1} (n+1-s)^(a-1) ds      (h = 1)
+# Product trapezoid (corrector): f replaced by its piecewise-linear interpolant,
+#   hat functions phi_j:  weight_j = 1/Gamma(a) * int (n+1-s)^(a-1) phi_j(s) ds
+#   j = 0 -> c_n,  1 <= j <= n -> a_{n-j},  j = n+1 -> 1/Gamma(a+2).
+# ---------------------------------------------------------------------------
+def _quad_weights(alpha, n):
+    """The same integrals in the lag variable u = n + 1 - s (kernel u^(a-1)),
+    so that the singular point is an endpoint u = 0 of the integration."""
+    mp = mpmath.mp
+    mp.dps = 40
+    al = mp.mpf(alpha)
+    G = mp.gamma(al)
+    ker = lambda u: u ** (al - 1)
+
+    def q0(psi):
+        # int_0^1 u^(a-1) psi(u) du with u = v^(1/a): (1/a) int_0^1 psi(v^(1/a)) dv,
+        # which takes the endpoint singularity out of the integrand.
+        return mp.quad(lambda v: psi(v ** (1 / al)), [0, 1]) / al
+
+    b = [q0(lambda u: 1) / G] + [mp.quad(ker, [m, m + 1]) / G for m in range(1, n + 1)]
+    # hat of node j = n - m is centred at u = m + 1 and spans [m, m + 2]
+    a = [((q0(lambda u: u) if m == 0 else mp.quad(lambda u: ker(u) * (u - m), [m, m + 1])) +
+          mp.quad(lambda u: ker(u) * (m + 2 - u), [m + 1, m + 2])) / G for m in range(n)]
+    c_n = mp.quad(lambda u: ker(u) * (u - n), [n, n + 1]) / G      # node j = 0: u in [n, n+1]
+    g = q0(lambda u: 1 - u) / G                                     # node j = n+1: u in [0, 1]
+    return b, a, c_n, g
+
+
+@pytest.mark.parametrize("alpha", ALPHAS)
+def test_weights_match_product_integration_quadrature(alpha):
+    n = 12
+    bq, aq, cq, gq = _quad_weights(alpha, n)
+    b, a, c, g = oracle.weights(alpha, n)
+    for m in range(n + 1):
+        assert abs(b[m] - float(bq[m])) <= 1e-14 * abs(float(bq[m])), (m, b[m], bq[m])
+    for m in range(n):
+        assert abs(a[m] - float(aq[m])) <= 1e-14 * abs(float(aq[m])), (m, a[m], aq[m])
+    assert abs(c[n] - float(cq)) <= 1e-14 * abs(float(cq))
+    assert abs(g - float(gq)) <= 1e-14 * abs(float(gq))
+
+
+@pytest.mark.parametrize("alpha", ALPHAS)
+def test_weights_high_precision_at_large_lag(alpha):
+    """Binary128 evaluation keeps large-lag cancellation out of FP64: compare
+    with 60-digit mpmath values of the definitions, within 1 ulp."""
+    mp = mpmath.mp
+    mp.dps = 60
+    M = 1 << 18
+    b, a, c, g = oracle.weights(alpha, M)
+    al = mp.mpf(alpha)
+    for m in [0, 1, 2, 3, 31, 32, 33, 1000, 65535, 1 << 17, M - 1, M]:
+        q = mp.mpf(m)
+        be = ((q + 1) ** al - (q ** al if m else 0)) / mp.gamma(al + 1)
+        ae = ((q + 2) ** (al + 1) - 2 * (q + 1) ** (al + 1) + (q ** (al + 1) if m else 0)) / mp.gamma(al + 2)
+        ce = ((q ** (al + 1) if m else 0) - (q - al) * (q + 1) ** al) / mp.gamma(al + 2)
+        for got, ex in ((b[m], be), (a[m], ae), (c[m], ce)):
+            ex = float(ex)
+            assert abs(got - ex) <= math.ulp(ex), (alpha, m, got, ex)
+
+
+def test_weights_alpha_one_are_rectangle_and_trapezoid():
+    b, a, c, g = oracle.weights(1.0, 1 << 12)
+    assert np.all(b == 1.0) and np.all(a == 1.0) and np.all(c == 0.5) and g == 0.5
+
+
+def test_weights_reject_bad_alpha():
+    for al in (0.0, -0.5, 1.5, float("nan")):
+        with pytest.raises(ValueError):
+            oracle.weights(al, 4)
+
+
+# ---------------------------------------------------------------------------
+# Exact solutions.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("alpha", [0.3, 0.5, 0.9, 0.98, 1.0])
+@pytest.mark.parametrize("h", [0.1, 0.013])
+def test_linear_forcing_is_exact(alpha, h):
+    """The product trapezoid integrates a linear f exactly: for f = q0 + q1 t,
+    y(t) = y0 + q0 t^a/Gamma(a+1) + q1 t^(a+1)/Gamma(a+2) at every grid point."""
+    N, q0, q1, y0 = 300, 1.3, -0.7, 0.25
+    Y, YP = oracle.solve("linear", alpha, h, N, [0.0, q0, q1], [y0])
+    t = np.arange(N + 1) * h
+    ex = y0 + q0 * t ** alpha / math.gamma(alpha + 1) + q1 * t ** (alpha + 1) / math.gamma(alpha + 2)
+    # Rounding only: a length-N FP64 sum errs by at most ~N * eps * sum|terms|.
+    tol = 8 * N * np.finfo(float).eps * np.abs(ex).max()
+    assert np.max(np.abs(Y[:, 0] - ex)) < tol
+
+
+@pytest.mark.parametrize("alpha", [0.3, 0.5, 0.9, 1.0])
+def test_constant_forcing_predictor_is_exact(alpha):
+    """The product rectangle (eq. 2) integrates a constant f exactly."""
+    N, h, q0, y0 = 257, 0.02, 2.5, -0.5
+    Y, YP = oracle.solve("linear", alpha, h, N, [0.0, q0, 0.0], [y0])
+    t = np.arange(N + 1) * h
+    ex = y0 + q0 * t ** alpha / math.gamma(alpha + 1)
+    tol = 8 * N * np.finfo(float).eps * np.abs(ex).max()
+    assert np.max(np.abs(YP[1:, 0] - ex[1:])) < tol
+    assert np.max(np.abs(Y[1:, 0] - ex[1:])) < tol
+
+
+def _manufactured_params(alpha, beta, gam=0.0):
+    c1, c2, c3, e0 = 1.0, -0.5, 0.3, 0.2
+    q0 = c1 * math.gamma(1 + alpha)
+    q1 = c2 * math.gamma(2 + alpha)
+    q2 = c3 * math.gamma(3 + alpha) / 2.0
+    return [q0, q1, q2, beta, gam, e0, c1, c2, c3], e0, (c1, c2, c3)
+
+
+def _manufactured_error(alpha, beta, h, T=1.0, gam=0.0):
+    p, e0, (c1, c2, c3) = _manufactured_params(alpha, beta, gam)
+    N = int(round(T / h))
+    Y, _ = oracle.solve("manufactured", alpha, h, N, p, [e0])
+    t = np.arange(N + 1) * h
+    ye = e0 + c1 * t ** alpha + c2 * t ** (1 + alpha) + c3 * t ** (2 + alpha)
+    return np.abs(Y[:, 0] - ye).max()
+
+
+@pytest.mark.parametrize("alpha", [0.3, 0.5, 0.8, 0.95, 1.0])
+def test_convergence_order_manufactured(alpha):
+    """D^a y in C^2 gives error O(h^min(2, 1+a)) (Diethelm-Ford-Freed, the
+    scheme's published error analysis); observed on the finest pair, +-0.1."""
+    e1 = _manufactured_error(alpha, -1.0, 2.0 ** -9, gam=-0.5)
+    e2 = _manufactured_error(alpha, -1.0, 2.0 ** -10, gam=-0.5)
+    order = math.log2(e1 / e2)
+    assert abs(order - min(2.0, 1.0 + alpha)) < 0.1, order
+
+
+def _mittag_leffler(alpha, z):
+    mp = mpmath.mp
+    mp.dps = 60
+    z = mp.mpf(z)
+    s, k = mp.mpf(0), 0
+    while True:
+        term = z ** k / mp.gamma(alpha * k + 1)
+        s += term
+        if k > 10 and abs(term) < mp.mpf(10) ** -40:
+            break
+        k += 1
+    return float(s)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.9, 1.0])
+@pytest.mark.parametrize("lam", [-1.0, -2.0, 0.5])
+def test_mittag_leffler(alpha, lam):
+    """D^a y = lam y has y = y0 E_a(lam t^a).  The error falls as h falls, and
+    at alpha = 1 (E_1 = exp) it falls at order 2."""
+    T, y0 = 2.0, 1.0
+    ts = np.array([0.5, 1.0, 1.5, 2.0])
+    ex = np.array([y0 * _mittag_leffler(alpha, lam * t ** alpha) for t in ts])
+    errs = []
+    for h in [2.0 ** -5, 2.0 ** -7, 2.0 ** -9]:
+        N = int(round(T / h))
+        Y, _ = oracle.solve("linear", alpha, h, N, [lam, 0.0, 0.0], [y0])
+        idx = np.rint(ts / h).astype(int)
+        errs.append(np.max(np.abs(Y[idx, 0] - ex) / np.abs(ex)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 2e-3
+    if alpha == 1.0:
+        assert abs(math.log2(errs[1] / errs[2]) / 2.0 - 2.0) < 0.1
+
+
+def _integral_trapezoid(system, h, N, p, y0):
+    """alpha = 1: rectangle predictor / trapezoid corrector in integral form,
+    written independently of the oracle's weight machinery."""
+    d = oracle.dim(system)
+    y0 = np.asarray(y0, dtype=np.float64)
+    Y = np.empty((N + 1, d)); Y[0] = y0
+    Fs = [oracle.rhs(system, 1.0, p, 0.0, y0)]
+    run = Fs[0].copy()                 # sum_{k<=n} f_k
+    for n in range(N):
+        t1 = (n + 1) * h
+        yp = y0 + h * run
+        fp = oracle.rhs(system, 1.0, p, t1, yp)
+        tail = run - Fs[0]
+        y = y0 + h * (0.5 * Fs[0] + tail + 0.5 * fp)
+        Y[n + 1] = y
+        Fs.append(oracle.rhs(system, 1.0, p, t1, y))
+        run = run + Fs[-1]
+    return Y
+
+
+@pytest.mark.parametrize("system,p,y0", [
+    ("lorenz", [10.0, 28.0, 8.0 / 3.0], [0.1, 0.1, 0.1]),
+    ("linear", [-1.5, 0.2, 0.1], [1.0]),
+])
+def test_alpha_one_is_integral_form_trapezoid(system, p, y0):
+    h, N = 0.01, 400
+    Yo, _ = oracle.solve(system, 1.0, h, N, p, y0)
+    Yt = _integral_trapezoid(system, h, N, p, y0)
+    scale = np.maximum(np.abs(Yt), 1e-3 * np.abs(Yt).max())
+    # Summation order differs from the oracle's (running sum vs index loop).
+    assert np.max(np.abs(Yo - Yt) / scale) < 1e-11
+
+
+def test_alpha_one_order_two_to_exponential():
+    errs = []
+    for h in [2.0 ** -6, 2.0 ** -7, 2.0 ** -8]:
+        N = int(round(1.0 / h))
+        Y, _ = oracle.solve("linear", 1.0, h, N, [-1.0, 0.0, 0.0], [1.0])
+        errs.append(abs(Y[-1, 0] - math.exp(-1.0)))
+    o1, o2 = math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])
+    assert abs(o1 - 2.0) < 0.1 and abs(o2 - 2.0) < 0.1
+
+
+# ---------------------------------------------------------------------------
+# Right-hand sides of the workload systems: equilibria, Jacobian consistency,
+# and the Lorenz flow's constant divergence -(sigma + 1 + beta).
+# ---------------------------------------------------------------------------
+def _equilibria():
+    s, r, bt = 10.0, 28.0, 8.0 / 3.0
+    q = math.sqrt(bt * (r - 1))
+    ca, cb, cc = 35.0, 3.0, 28.0
+    w = math.sqrt(cb * (2 * cc - ca))
+    ra, rb, rc = 0.2, 0.2, 5.7
+    ys = [(-rc + sg * math.sqrt(rc * rc - 4 * ra * rb)) / (2 * ra) for sg in (1, -1)]
+    fa, fb, fc = 3.0, 0.1, 1.0
+    xf = math.sqrt(1 - fb * (fa + 1 / fc))
+    return [
+        ("lorenz", [s, r, bt], [[0, 0, 0], [q, q, r - 1], [-q, -q, r - 1]]),
+        ("chen", [ca, cb, cc], [[0, 0, 0], [w, w, 2 * cc - ca], [-w, -w, 2 * cc - ca]]),
+        ("rossler", [ra, rb, rc], [[-ra * y, y, -y] for y in ys]),
+        ("financial", [fa, fb, fc], [[0, 1 / fb, 0], [xf, fa + 1 / fc, -xf / fc], [-xf, fa + 1 / fc, xf / fc]]),
+    ]
+
+
+@pytest.mark.parametrize("system,p,points", _equilibria())
+def test_rhs_vanishes_at_equilibria(system, p, points):
+    for y in points:
+        f = oracle.rhs(system, 0.9, p, 0.37, y)
+        assert np.max(np.abs(f)) < 1e-12 * (1 + np.max(np.abs(y))) ** 2, (system, y, f)
+
+
+@pytest.mark.parametrize("system,p", [("lorenz", [10.0, 28.0, 8 / 3]), ("chen", [35.0, 3.0, 28.0]),
+                                      ("rossler", [0.2, 0.2, 5.7]), ("financial", [3.0, 0.1, 1.0]),
+                                      ("linear", [-1.2, 0.3, 0.5]), ("manufactured", None)])
+def test_jacobians_match_central_differences(system, p):
+    alpha = 0.8
+    if system == "manufactured":
+        p, _, _ = _manufactured_params(alpha, -1.0, -0.5)
+    rng = np.random.default_rng(1611)
+    d = oracle.dim(system)
+    for _ in range(4):
+        y = rng.uniform(-2, 2, d)
+        t = rng.uniform(0.1, 2.0)
+        J, Q = oracle.jac(system, alpha, p, t, y)
+        for j in range(d):
+            e = np.zeros(d); e[j] = 1e-6
+            fd = (oracle.rhs(system, alpha, p, t, y + e) - oracle.rhs(system, alpha, p, t, y - e)) / 2e-6
+            np.testing.assert_allclose(J[:, j], fd, rtol=1e-6, atol=1e-6)
+        for j in range(len(p)):
+            pp, pm = list(p), list(p)
+            pp[j] += 1e-6; pm[j] -= 1e-6
+            fd = (oracle.rhs(system, alpha, pp, t, y) - oracle.rhs(system, alpha, pm, t, y)) / 2e-6
+            np.testing.assert_allclose(Q[:, j], fd, rtol=1e-6, atol=1e-6)
+
+
+def test_lorenz_divergence_is_constant():
+    s, r, bt = 10.0, 28.0, 8.0 / 3.0
+    rng = np.random.default_rng(1611)
+    for _ in range(5):
+        y = rng.uniform(-20, 20, 3)
+        div = 0.0
+        for j in range(3):
+            e = np.zeros(3); e[j] = 1e-5
+            div += (oracle.rhs("lorenz", 1.0, [s, r, bt], 0.0, y + e)[j]
+                    - oracle.rhs("lorenz", 1.0, [s, r, bt], 0.0, y - e)[j]) / 2e-5
+        assert abs(div + (s + 1 + bt)) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# History sums and the tangent-linear gradient.
+# ---------------------------------------------------------------------------
+def test_history_brute_force_and_solve_identity():
+    rng = np.random.default_rng(1611)
+    alpha, n = 0.73, 17
+    b, a, c, g = oracle.weights(alpha, n + 1)
+    F = rng.standard_normal((n + 1, 4))
+    P, C = oracle.history(b, a, c, F, n, 0, n + 1)
+    for col in range(4):
+        sp = sum(b[n - k] * F[k, col] for k in range(n + 1))
+        sc = c[n] * F[0, col] + sum(a[n - k] * F[k, col] for k in range(1, n + 1))
+        assert abs(P[col] - sp) < 1e-14 * (1 + abs(sp)) and abs(C[col] - sc) < 1e-14 * (1 + abs(sc))
+    # the solve's own predictor equals y0 + h^a * history sum
+    h = 0.01
+    Y, YP, Fs = oracle.solve("lorenz", alpha, h, 40, [10.0, 28.0, 8 / 3], [0.1, 0.2, 0.3], return_f=True)
+    b, a, c, g = oracle.weights(alpha, 40)
+    for nn in (0, 5, 39):
+        P, C = oracle.history(b, a, c, Fs, nn, 0, nn + 1)
+        np.testing.assert_allclose(YP[nn + 1], np.array([0.1, 0.2, 0.3]) + h ** alpha * P, rtol=1e-14)
+
+
+@pytest.mark.parametrize("system,p,y0,alpha,h,N", [
+    ("lorenz", [10.0, 28.0, 8.0 / 3.0], [0.1, 0.1, 0.1], 0.98, 0.01, 60),
+    ("financial", [3.0, 0.1, 1.0], [2.0, 3.0, 2.0], 0.95, 0.01, 80),
+    ("rossler", [0.2, 0.2, 5.7], [0.5, -0.3, 0.1], 0.9, 0.01, 80),
+    ("chen", [35.0, 3.0, 28.0], [-9.0, -5.0, 14.0], 0.9, 0.001, 60),
+    ("manufactured", None, None, 0.6, 0.02, 50),
+])
+def test_tangent_matches_central_differences(system, p, y0, alpha, h, N):
+    if system == "manufactured":
+        p, e0, _ = _manufactured_params(alpha, -1.0, -0.5)
+        y0 = [e0 + 0.1]
+    d = oracle.dim(system)
+    rng = np.random.default_rng(8678)
+    Y, _ = oracle.solve(system, alpha, h, N, p, y0)
+    target = Y + 0.05 * rng.standard_normal(Y.shape)
+    # loss = mean (y - target)^2  ->  dL/dy_n = 2 (y_n - target_n) / size
+    dLdY = 2.0 * (Y - target) / Y.size
+    dp, dy0 = oracle.tangent(system, alpha, h, N, p, y0, dLdY)
+
+    def loss(pp, yy):
+        Yv, _ = oracle.solve(system, alpha, h, N, pp, yy)
+        return np.mean((Yv - target) ** 2)
+
+    theta = list(p) + list(y0)
+    for j in range(len(theta)):
+        delta = 1e-6 * max(1.0, abs(theta[j]))
+        tp, tm = list(theta), list(theta)
+        tp[j] += delta; tm[j] -= delta
+        n_p = len(p)
+        fd = (loss(tp[:n_p], tp[n_p:]) - loss(tm[:n_p], tm[n_p:])) / (2 * delta)
+        an = dp[j] if j < n_p else dy0[j - n_p]
+        assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3) + 1e-10, (system, j, an, fd)
+
+
+# ---------------------------------------------------------------------------
+# Mutation tests: plant a mistake in a copy of the oracle, on the CPU, and
+# check that the pins above reject it.
+# ---------------------------------------------------------------------------
+MUTANTS = {
+    "b_sign_plus": ("b[m] = (double)((pm1_a - pm_a) / ga1);", "b[m] = (double)((pm1_a + pm_a) / ga1);"),
+    "a_second_difference_sign": ("(pm2_a1 - 2 * pm1_a1 + pm_a1)", "(pm2_a1 - 2 * pm1_a1 - pm_a1)"),
+    "c_replaced_by_a": ("double s = c[n] * F[i];", "double s = a[n] * F[i];"),
+    "dropped_g_term": ("hh * (s + g * fp[i]);", "hh * (s);"),
+    "predictor_lag_shift": ("s += b[n - k] * F[k * d + i];", "s += b[n - k + 1] * F[k * d + i];"),
+    "corrector_lag_shift": ("s += a[n - k] * F[k * d + i];", "s += a[n - k + 1] * F[k * d + i];"),
+    "hhat_power": ("double hh = pow(h, alpha);\n  double yp[3]", "double hh = pow(h, alpha + 1.0);\n  double yp[3]"),
+    "time_index": ("double t1 = (double)(n + 1) * h;\n    for (int i = 0; i < d; ++i) {             /* predictor",
+                   "double t1 = (double)n * h;\n    for (int i = 0; i < d; ++i) {             /* predictor"),
+    "lorenz_transposed": ("f[1] = y[0] * (p[1] - y[2]) - y[1];", "f[1] = y[1] * (p[1] - y[2]) - y[0];"),
+}
+
+
+def _pins_pass():
+    """Runs a compact version of the pins; returns False at the first failure."""
+    checks = [
+        lambda: test_weights_match_product_integration_quadrature(0.5),
+        lambda: test_linear_forcing_is_exact(0.5, 0.1),
+        lambda: test_constant_forcing_predictor_is_exact(0.5),
+        lambda: test_convergence_order_manufactured(0.5),
+        lambda: test_alpha_one_is_integral_form_trapezoid("lorenz", [10.0, 28.0, 8.0 / 3.0], [0.1, 0.1, 0.1]),
+        lambda: test_mittag_leffler(0.9, -1.0),
+        test_lorenz_divergence_is_constant,
+    ] + [lambda e=e: test_rhs_vanishes_at_equilibria(*e) for e in _equilibria()]
+    for chk in checks:
+        try:
+            chk()
+        except AssertionError:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutants_are_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    path = oracle.compile_source(src.replace(old, new), str(tmp_path / f"mut_{name}.so"))
+    with oracle.use_library(path):
+        assert not _pins_pass(), f"mutant {name} survived every pin"
+
+
+def test_unmutated_oracle_passes_compact_pins():
+    assert _pins_pass()
