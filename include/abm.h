@@ -1,0 +1,185 @@
+/*
+ * abm.h - C ABI of the GB300 (sm_103a) fractional Adams-Bashforth-Moulton
+ * history-convolution library.
+ *
+ * The method (arXiv 1611.08678, Sec. 2): solve the Caputo fractional ODE
+ *     D_*^alpha y(t) = f(t, y(t)),  y(0) = y0,  t in [0, T],  alpha in (0, 1]
+ * (eq. (1); alpha = 0 is excluded as degenerate) on the grid t_n = n h,
+ * h = T/N, with the predictor of eq. (2)
+ *     y^P_{n+1} = y0 + h^alpha sum_{k=0..n} b_{n-k} f_k
+ * and the corrector that follows it
+ *     y_{n+1} = y0 + h^alpha (c_n f_0 + sum_{k=1..n} a_{n-k} f_k
+ *                             + f(t_{n+1}, y^P_{n+1}) / Gamma(alpha+2)),
+ * f_k = f(t_k, y_k), with the weights b_m, a_m, c_m defined in Sec. 2 (the
+ * printed '+' inside b_m is read as '-', the product-rectangle weight).
+ * Every step of the computation runs in this library's CUDA kernels; the
+ * caller supplies f by choosing one of the built-in systems below.
+ *
+ * Conventions for every entry point:
+ *  - Return value: an abm_status.  Argument errors are detected on the host
+ *    and returned synchronously, before anything is launched.
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream) and is asynchronous.  Errors found on the
+ *    device (non-finite state, a bounded wait that ran out) are recorded in
+ *    the plan's status word and returned by abm_plan_sync().
+ *  - Device pointers must point to memory of the device that was current
+ *    when the plan was created.  The caller owns every buffer it passes; the
+ *    plan owns its internal workspace (weights, f history, partial sums).
+ *  - A plan is not thread-safe; calls that use one plan must be serialised
+ *    on one stream.
+ *  - abm_last_error() returns a human-readable message for the last failure.
+ */
+#ifndef ABM_H_
+#define ABM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ABM_OK = 0,
+  ABM_ERR_INVALID_ARG = 1, /* rejected on the host, nothing launched            */
+  ABM_ERR_CUDA = 2,        /* a CUDA runtime call failed                        */
+  ABM_ERR_OOM = 3,         /* device allocation failed                          */
+  ABM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                */
+  ABM_ERR_NONFINITE = 5,   /* a state or f value became NaN/Inf                 */
+  ABM_ERR_UNSUPPORTED = 6  /* valid request this build does not implement       */
+} abm_status;
+
+/* Built-in right-hand sides f(t, y) with their dimension d and parameters:
+ *  LINEAR       d=1  (lam, q0, q1)            f = lam y + q0 + q1 t
+ *  MANUFACTURED d=1  (q0,q1,q2,beta,gam,e0,c1,c2,c3)
+ *                    f = q0 + q1 t + q2 t^2 + beta r + gam r^3,
+ *                    r = y - (e0 + c1 t^a + c2 t^(1+a) + c3 t^(2+a))
+ *  LORENZ       d=3  (sigma, rho, beta)  x'=sigma(y-x), y'=x(rho-z)-y, z'=xy-beta z
+ *  CHEN         d=3  (a, b, c)           x'=a(y-x), y'=(c-a)x-xz+cy, z'=xy-bz
+ *  ROSSLER      d=3  (a, b, c)           x'=-y-z, y'=x+ay, z'=b+z(x-c)
+ *  FINANCIAL    d=3  (a, b, c)           x'=z+(y-a)x, y'=1-by-x^2, z'=-x-cz     */
+typedef enum {
+  ABM_SYS_LINEAR = 0,
+  ABM_SYS_MANUFACTURED = 1,
+  ABM_SYS_LORENZ = 2,
+  ABM_SYS_CHEN = 3,
+  ABM_SYS_ROSSLER = 4,
+  ABM_SYS_FINANCIAL = 5
+} abm_system;
+
+/* Arithmetic of the far-history part (lags older than the current time tile).
+ * The weights, the j = 0 and j = n+1 terms, the near lags and the PECE state
+ * update are FP64 in every mode. */
+typedef enum {
+  ABM_PREC_FP64 = 0,      /* far history in FP64                                 */
+  ABM_PREC_FP32_FAR = 1,  /* far history: FP32 operands, FP32 products/accumulate
+                             within a lag block, blocks combined in FP64         */
+  ABM_PREC_BF16X3_FAR = 2 /* far history: each operand split into three BF16
+                             pieces, the three largest cross products on the
+                             tensor cores with FP32 accumulation, blocks in FP64 */
+} abm_precision;
+
+typedef struct abm_plan_s* abm_plan;
+
+typedef struct {
+  abm_precision prec;  /* far-history arithmetic (batched path)                 */
+  int n_max;           /* largest N any call will use (workspace is sized once)  */
+  int max_batch;       /* largest M for abm_solve_batched (0: single only)       */
+  int tile_B;          /* time-tile length B (0 = library default)               */
+  int far_ctas;        /* CTAs of the single-trajectory far kernel (0 = auto)    */
+  int use_graph;       /* 1: capture the launch sequence in a CUDA graph and
+                          replay it while the arguments' shapes are unchanged    */
+  long long spin_timeout_cycles; /* bound of every device-side wait in clock
+                          cycles (0 = default, about two seconds)                */
+  int test_withhold_tile; /* testing only, 0 = off.  k > 0: in abm_solve the far
+                          CTAs never publish tile k-1, so the near CTA's wait
+                          runs out and the call reports ABM_ERR_TIMEOUT           */
+  int reserved[8];     /* must be zero                                            */
+} abm_plan_opts;
+
+/* Fills *o with the defaults (FP64, n_max = 0, tile_B = 0 ...). */
+void abm_plan_opts_default(abm_plan_opts* o);
+
+/* Dimension d and parameter count of a system; -1 for an unknown system. */
+int abm_system_dim(abm_system sys);
+int abm_system_nparams(abm_system sys);
+
+/* Creates a plan for one system.  Allocates the workspace for n_max steps and
+ * max_batch trajectories on the current device.  ABM_ERR_INVALID_ARG for
+ * n_max < 1, negative sizes or nonzero reserved fields; ABM_ERR_OOM when the
+ * workspace does not fit. */
+abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o);
+
+/* Frees the plan and its workspace (synchronises the device first). */
+abm_status abm_plan_destroy(abm_plan p);
+
+/* Synchronises `stream`, then returns and clears the plan's device status
+ * word (ABM_OK, ABM_ERR_NONFINITE or ABM_ERR_TIMEOUT).  If `where` is not
+ * NULL it receives the packed detail (trajectory index << 32 | step). */
+abm_status abm_plan_sync(abm_plan p, void* stream, int64_t* where);
+
+/* Message of the last failure on this plan (owned by the plan, valid until
+ * the next call on it).  Never NULL. */
+const char* abm_last_error(abm_plan p);
+
+/* A1 - weight generation (Sec. 2 weight definitions; the CUDA variant of the
+ * paper's per-thread weight precompute, Sec. 4 "CUDA simulations").
+ * Writes b[m], a[m], c[m] for m = 0..M (device arrays of M+1 doubles) for
+ * this alpha in FP64.  Large lags use cancellation-free series, small lags a
+ * 16-point Gauss-Legendre quadrature of the product-integration kernels.
+ * alpha in (0, 1], M >= 0. */
+abm_status abm_weights(abm_plan p, double alpha, int M, double* b, double* a, double* c,
+                       void* stream);
+
+/* Single trajectory (the paper's ParABM problem, Sec. 3 Fig. 2 inputs
+ * T = N h, N, y0).  alpha in (0, 1], h > 0 finite, 1 <= N <= n_max.
+ * params: host array of abm_system_nparams(sys) doubles; y0: host array of d
+ * doubles (finite).  Y: device array of (N+1)*d doubles, row n = y_n
+ * (Y[0..d-1] = y0).  YP (may be NULL): device array of (N+1)*d doubles that
+ * receives the predictor values y^P_n (row 0 = y0).  FP64 throughout: the
+ * far history is split across the GPU's SMs, the near lags and the
+ * sequential PECE steps run in one CTA. */
+abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* params,
+                     const double* y0, double* Y, double* YP, void* stream);
+
+/* Batched trajectories (independent problems with their own alpha, h, N,
+ * parameters and initial values).  alpha, h, N: HOST arrays of M entries
+ * (they drive the scheduling: trajectories are grouped by alpha and ordered
+ * by N on the host).  params: device array M x nparams; y0: device M x d.
+ * Y: device array M x ldY x d with ldY >= max(N)+1; trajectory i's rows
+ * 0..N[i] are written, the rest are left untouched.  YP (may be NULL) has
+ * the layout of Y and receives y^P.  The plan's precision selects the
+ * far-history arithmetic.  1 <= M <= max_batch, 1 <= N[i] <= n_max. */
+abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const double* h,
+                             const int* N, const double* params, const double* y0, double* Y,
+                             long long ldY, double* YP, void* stream);
+
+/* Adjoint of abm_solve_batched (the discrete adjoint of exactly the scheme
+ * above; the paper has no adjoint).  The arguments alpha .. ldY must be those
+ * of a completed abm_solve_batched call on this plan whose outputs Y and YP
+ * (both required here) are still intact.  dLdY: device array with the layout
+ * of Y holding the partial derivatives of a scalar loss with respect to every
+ * y_n (rows beyond N[i] ignored).  Outputs (device): dparams M x nparams and
+ * dy0 M x d, the total derivatives of the loss.  The Jacobians of f are
+ * recomputed from Y and YP; no Jacobian is stored. */
+abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, const int* N,
+                       const double* params, const double* y0, const double* Y, const double* YP,
+                       long long ldY, const double* dLdY, double* dparams, double* dy0,
+                       void* stream);
+
+/* Far-history sums alone (the A2 contraction, exposed for parity tests and
+ * roofline measurement).  F: device, rows x cols row-major FP64 history
+ * (row k = f_k).  For targets n = s..s+B-1 and history rows k in [k_lo, k_hi)
+ * with 1 <= k_lo <= k_hi <= s:
+ *   P[i][col] = sum_k b_{s+i-k} F[k][col],  C[i][col] = sum_k a_{s+i-k} F[k][col]
+ * (P, C: device B x cols).  Uses the plan's precision and this alpha's
+ * weights. */
+abm_status abm_far_history(abm_plan p, double alpha, const double* F, long long rows,
+                           long long cols, long long s, int B, long long k_lo, long long k_hi,
+                           double* P, double* C, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABM_H_ */

@@ -1,0 +1,229 @@
+"""ctypes binding of libabm_gb300.so (include/abm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch provides device memory and streams.  There is no CPU path:
+if the library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libabm_gb300.so")
+
+SYSTEMS = {"linear": 0, "manufactured": 1, "lorenz": 2, "chen": 3, "rossler": 4, "financial": 5}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2}
+STATUS = {0: "ABM_OK", 1: "ABM_ERR_INVALID_ARG", 2: "ABM_ERR_CUDA", 3: "ABM_ERR_OOM",
+          4: "ABM_ERR_TIMEOUT", 5: "ABM_ERR_NONFINITE", 6: "ABM_ERR_UNSUPPORTED"}
+
+# Every symbol include/abm.h declares (checked by the CPU test suite).
+EXPORTS = ["abm_plan_opts_default", "abm_system_dim", "abm_system_nparams", "abm_plan_create",
+           "abm_plan_destroy", "abm_plan_sync", "abm_last_error", "abm_weights", "abm_solve",
+           "abm_solve_batched", "abm_adjoint", "abm_far_history"]
+
+
+class AbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("n_max", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("tile_B", ctypes.c_int), ("far_ctas", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("spin_timeout_cycles", ctypes.c_longlong), ("test_withhold_tile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _dp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+
+
+def load(path: str = LIB_PATH):
+    """Loads the library (builds it first when sources are newer).  Raises if
+    it cannot be built or loaded; there is no fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing")
+        lib = ctypes.CDLL(path)
+        I, LL, D = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+        lib.abm_plan_opts_default.argtypes = [ctypes.POINTER(PlanOpts)]
+        lib.abm_plan_opts_default.restype = None
+        lib.abm_system_dim.argtypes = [I]
+        lib.abm_system_nparams.argtypes = [I]
+        lib.abm_plan_create.argtypes = [ctypes.POINTER(_vp), I, ctypes.POINTER(PlanOpts)]
+        lib.abm_plan_destroy.argtypes = [_vp]
+        lib.abm_plan_sync.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
+        lib.abm_last_error.argtypes = [_vp]
+        lib.abm_last_error.restype = ctypes.c_char_p
+        lib.abm_weights.argtypes = [_vp, D, I, _vp, _vp, _vp, _vp]
+        lib.abm_solve.argtypes = [_vp, D, D, I, _dp, _dp, _vp, _vp, _vp]
+        lib.abm_solve_batched.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
+        lib.abm_adjoint.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp, _vp, _vp]
+        lib.abm_far_history.argtypes = [_vp, D, _vp, LL, LL, LL, I, LL, LL, _vp, _vp, _vp]
+        for name in EXPORTS:
+            if name not in ("abm_plan_opts_default", "abm_last_error", "abm_system_dim", "abm_system_nparams"):
+                getattr(lib, name).restype = I
+        _lib = lib
+        return lib
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the ABM library has no CPU path")
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """One plan = one system, workspace for n_max steps and max_batch trajectories."""
+
+    def __init__(self, system: str, n_max: int, max_batch: int = 0, prec: str = "fp64", tile_B: int = 0,
+                 far_ctas: int = 0, use_graph: bool = False, spin_timeout_cycles: int = 0,
+                 test_withhold_tile: int = 0):
+        self.lib = load()
+        self.system = system
+        self.d = self.lib.abm_system_dim(SYSTEMS[system])
+        self.np = self.lib.abm_system_nparams(SYSTEMS[system])
+        self.prec = prec
+        o = PlanOpts()
+        self.lib.abm_plan_opts_default(ctypes.byref(o))
+        o.prec = PRECISIONS[prec]
+        o.n_max = int(n_max)
+        o.max_batch = int(max_batch)
+        o.tile_B = int(tile_B)
+        o.far_ctas = int(far_ctas)
+        o.use_graph = int(bool(use_graph))
+        o.spin_timeout_cycles = int(spin_timeout_cycles)
+        o.test_withhold_tile = int(test_withhold_tile)
+        h = _vp()
+        st = self.lib.abm_plan_create(ctypes.byref(h), SYSTEMS[system], ctypes.byref(o))
+        if st != 0:
+            raise AbmError(st, "abm_plan_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.abm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            raise AbmError(st, f"{what}: {self.lib.abm_last_error(self.h).decode()}")
+
+    def sync(self, stream=None):
+        where = ctypes.c_int64(0)
+        st = self.lib.abm_plan_sync(self.h, _stream_ptr(stream), ctypes.byref(where))
+        self._check(st, "device status")
+        return where.value
+
+    # -- A1 --
+    def weights(self, alpha: float, M: int, stream=None):
+        torch = _torch()
+        b, a, c = (torch.empty(M + 1, dtype=torch.float64, device="cuda") for _ in range(3))
+        self._check(self.lib.abm_weights(self.h, float(alpha), int(M), _dptr(b), _dptr(a), _dptr(c),
+                                         _stream_ptr(stream)), "abm_weights")
+        return b, a, c
+
+    # -- A2 alone (FP64 plans) --
+    def far_history(self, alpha, F, s, B, k_lo, k_hi, stream=None):
+        torch = _torch()
+        rows, cols = F.shape
+        P = torch.empty(B, cols, dtype=torch.float64, device="cuda")
+        C = torch.empty(B, cols, dtype=torch.float64, device="cuda")
+        self._check(self.lib.abm_far_history(self.h, float(alpha), _dptr(F), rows, cols, int(s), int(B),
+                                             int(k_lo), int(k_hi), _dptr(P), _dptr(C), _stream_ptr(stream)),
+                    "abm_far_history")
+        return P, C
+
+    # -- single trajectory --
+    def solve(self, alpha, h, N, params, y0, Y=None, YP=None, want_yp=False, stream=None, sync=True):
+        torch = _torch()
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        y = np.ascontiguousarray(y0, dtype=np.float64)
+        if p.size != self.np or y.size != self.d:
+            raise ValueError("params / y0 have the wrong size for this system")
+        if Y is None:
+            Y = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
+        if YP is None and want_yp:
+            YP = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
+        st = self.lib.abm_solve(self.h, float(alpha), float(h), int(N), p.ctypes.data_as(_dp),
+                                y.ctypes.data_as(_dp), _dptr(Y), _dptr(YP), _stream_ptr(stream))
+        self._check(st, "abm_solve")
+        if sync:
+            self.sync(stream)
+        return (Y, YP) if want_yp or YP is not None else Y
+
+    # -- batched --
+    def solve_batched(self, alpha, h, N, params, y0, Y=None, YP=None, want_yp=False, ldY=None, stream=None,
+                      sync=True):
+        """alpha, h, N: host sequences (scheduling); params (M, np), y0 (M, d):
+        torch CUDA tensors or host arrays (copied).  Returns Y (M, ldY, d)."""
+        torch = _torch()
+        al = np.ascontiguousarray(alpha, dtype=np.float64)
+        hh = np.ascontiguousarray(h, dtype=np.float64)
+        NN = np.ascontiguousarray(N, dtype=np.int32)
+        M = al.size
+        if not torch.is_tensor(params):
+            params = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float64), device="cuda")
+        if not torch.is_tensor(y0):
+            y0 = torch.as_tensor(np.ascontiguousarray(y0, dtype=np.float64), device="cuda")
+        params = params.contiguous()
+        y0 = y0.contiguous()
+        if ldY is None:
+            ldY = int(NN.max()) + 1
+        if Y is None:
+            Y = torch.zeros(M, ldY, self.d, dtype=torch.float64, device="cuda")
+        if YP is None and want_yp:
+            YP = torch.zeros(M, ldY, self.d, dtype=torch.float64, device="cuda")
+        st = self.lib.abm_solve_batched(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
+                                        NN.ctypes.data_as(_ip), _dptr(params), _dptr(y0), _dptr(Y), int(ldY),
+                                        _dptr(YP), _stream_ptr(stream))
+        self._check(st, "abm_solve_batched")
+        if sync:
+            self.sync(stream)
+        return (Y, YP) if want_yp or YP is not None else Y
+
+    def adjoint(self, alpha, h, N, params, y0, Y, YP, dLdY, stream=None, sync=True):
+        torch = _torch()
+        al = np.ascontiguousarray(alpha, dtype=np.float64)
+        hh = np.ascontiguousarray(h, dtype=np.float64)
+        NN = np.ascontiguousarray(N, dtype=np.int32)
+        M = al.size
+        dp = torch.empty(M, self.np, dtype=torch.float64, device="cuda")
+        dy0 = torch.empty(M, self.d, dtype=torch.float64, device="cuda")
+        st = self.lib.abm_adjoint(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
+                                  NN.ctypes.data_as(_ip), _dptr(params.contiguous()), _dptr(y0.contiguous()),
+                                  _dptr(Y), _dptr(YP), int(Y.shape[1]), _dptr(dLdY.contiguous()), _dptr(dp),
+                                  _dptr(dy0), _stream_ptr(stream))
+        self._check(st, "abm_adjoint")
+        if sync:
+            self.sync(stream)
+        return dp, dy0

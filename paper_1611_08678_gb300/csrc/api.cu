@@ -1,0 +1,476 @@
+// C ABI (include/abm.h): plans, argument checks, host-side scheduling and the
+// launch sequences of the single and batched paths.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "batched.cuh"
+#include "common.cuh"
+#include "single.cuh"
+
+namespace abm {
+// kernels (weights.cu, single.cu, batched.cu)
+cudaError_t launch_weights(double alpha, int M, double* b, double* a, double* c, double* g,
+                           cudaStream_t st);
+cudaError_t launch_weights_f32(int M, const double* b, const double* a, float* b32, float* a32,
+                               cudaStream_t st);
+
+cudaError_t launch_batched_setup(int sys, const BatchArgs& A, int n_tiles, cudaStream_t st);
+cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb,
+                                cudaStream_t st);
+cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, int n_active, long long s,
+                               cudaStream_t st);
+}  // namespace abm
+
+using namespace abm;
+
+namespace {
+
+constexpr int kDefaultB = 64;
+constexpr int kEventRing = 4;
+constexpr int kMaxWeightSets = 24;
+
+struct WeightSet {
+  double alpha = 0.0;
+  double *b = nullptr, *a = nullptr, *c = nullptr, *g = nullptr;
+  float *b32 = nullptr, *a32 = nullptr;
+  unsigned long long last_use = 0;
+};
+
+}  // namespace
+
+struct abm_plan_s {
+  abm_system sys;
+  int d = 0, np = 0;
+  abm_plan_opts o{};
+  int B = kDefaultB;
+  int device = 0, sms = 0;
+  int Mw = 0;                       // weights are generated for lags 0..Mw
+  std::vector<WeightSet> wsets;
+  unsigned long long use_clock = 0;
+  // single trajectory
+  double* F1 = nullptr;             // (n_max + B + 1) x d
+  double* far1 = nullptr;           // [2][B][2d]
+  double* part1 = nullptr;          // [2][G][B][2d]
+  unsigned int* tickets = nullptr;  // [2]
+  double* hhat1 = nullptr;          // 1
+  int G = 0;                        // CTAs of the stand-alone far kernel
+  int Gp = 0;                       // CTAs of the persistent single-trajectory kernel
+  double* ppartial = nullptr;       // [kPersistRing][Gp-1][kPersistB][2d]
+  unsigned long long* pflags = nullptr;  // [1 + kPersistRing]
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_near[kEventRing] = {}, ev_far[kEventRing] = {}, ev_start = nullptr;
+  // batched
+  int max_tiles = 0;
+  double* Fb = nullptr;
+  float* Fb32 = nullptr;
+  size_t fb_cap = 0;                // elements
+  double* farb = nullptr;
+  size_t farb_cap = 0;
+  TileDesc* d_tiles = nullptr;
+  double* d_h = nullptr;
+  int* d_N = nullptr;
+  double* d_hhat = nullptr;
+  double* d_balpha = nullptr;
+  double* d_bg = nullptr;           // gathered g per bucket
+  const double** d_bptr = nullptr;  // [4][kMaxWeightSets] b,a,c pointers
+  const float** d_b32ptr = nullptr; // [2][kMaxWeightSets]
+  unsigned long long* status = nullptr;
+  std::string err;
+};
+
+namespace {
+
+abm_status fail(abm_plan p, abm_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+abm_status cuda_fail(abm_plan p, cudaError_t e, const char* what) {
+  return fail(p, e == cudaErrorMemoryAllocation ? ABM_ERR_OOM : ABM_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(p, e_, what); \
+  } while (0)
+
+int sys_dim(abm_system s) {
+  switch (s) {
+    case ABM_SYS_LINEAR: case ABM_SYS_MANUFACTURED: return 1;
+    case ABM_SYS_LORENZ: case ABM_SYS_CHEN: case ABM_SYS_ROSSLER: case ABM_SYS_FINANCIAL: return 3;
+  }
+  return -1;
+}
+
+int sys_nparams(abm_system s) {
+  switch (s) {
+    case ABM_SYS_LINEAR: return 3;
+    case ABM_SYS_MANUFACTURED: return 9;
+    case ABM_SYS_LORENZ: case ABM_SYS_CHEN: case ABM_SYS_ROSSLER: case ABM_SYS_FINANCIAL: return 3;
+  }
+  return -1;
+}
+
+bool alpha_ok(double a) { return std::isfinite(a) && a > 0.0 && a <= 1.0; }
+
+// Weight vectors for one alpha (cached; least recently used set is reused).
+abm_status get_weights(abm_plan p, double alpha, cudaStream_t st, WeightSet** out) {
+  for (auto& w : p->wsets)
+    if (w.b && w.alpha == alpha) { w.last_use = ++p->use_clock; *out = &w; return ABM_OK; }
+  WeightSet* slot = nullptr;
+  for (auto& w : p->wsets)
+    if (!w.b) { slot = &w; break; }
+  if (!slot) {
+    slot = &p->wsets[0];
+    for (auto& w : p->wsets)
+      if (w.last_use < slot->last_use) slot = &w;
+  }
+  if (!slot->b) {
+    size_t n = (size_t)p->Mw + 1;
+    CK(cudaMalloc(&slot->b, n * sizeof(double)), "weights");
+    CK(cudaMalloc(&slot->a, n * sizeof(double)), "weights");
+    CK(cudaMalloc(&slot->c, n * sizeof(double)), "weights");
+    CK(cudaMalloc(&slot->g, sizeof(double)), "weights");
+    CK(cudaMalloc(&slot->b32, n * sizeof(float)), "weights");
+    CK(cudaMalloc(&slot->a32, n * sizeof(float)), "weights");
+  }
+  slot->alpha = alpha;
+  slot->last_use = ++p->use_clock;
+  CK(launch_weights(alpha, p->Mw, slot->b, slot->a, slot->c, slot->g, st), "weights kernel");
+  CK(launch_weights_f32(p->Mw, slot->b, slot->a, slot->b32, slot->a32, st), "weights f32");
+  *out = slot;
+  return ABM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void abm_plan_opts_default(abm_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->prec = ABM_PREC_FP64;
+}
+
+int abm_system_dim(abm_system sys) { return sys_dim(sys); }
+int abm_system_nparams(abm_system sys) { return sys_nparams(sys); }
+
+const char* abm_last_error(abm_plan p) { return p ? p->err.c_str() : "null plan"; }
+
+abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o) {
+  if (!out || !o) return ABM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (sys_dim(sys) < 0 || o->n_max < 1 || o->max_batch < 0 || o->tile_B < 0 || o->far_ctas < 0 ||
+      o->spin_timeout_cycles < 0 || (o->prec != ABM_PREC_FP64 && o->prec != ABM_PREC_FP32_FAR &&
+                                     o->prec != ABM_PREC_BF16X3_FAR))
+    return ABM_ERR_INVALID_ARG;
+  for (int r : o->reserved)
+    if (r) return ABM_ERR_INVALID_ARG;
+  if (o->tile_B && o->tile_B != 64 && o->tile_B != 32) return ABM_ERR_UNSUPPORTED;
+  if (o->prec == ABM_PREC_BF16X3_FAR) return ABM_ERR_UNSUPPORTED;
+  abm_plan p = new abm_plan_s();
+  p->sys = sys;
+  p->d = sys_dim(sys);
+  p->np = sys_nparams(sys);
+  p->o = *o;
+  p->B = o->tile_B ? o->tile_B : kDefaultB;
+  p->wsets.resize(kMaxWeightSets);
+  auto cleanup_fail = [&](abm_status s) { abm_plan_destroy(p); return s; };
+  if (cudaGetDevice(&p->device) != cudaSuccess) return cleanup_fail(ABM_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+    return cleanup_fail(ABM_ERR_CUDA);
+  p->G = o->far_ctas ? o->far_ctas : p->sms;
+  const int B = p->B, d = p->d;
+  const long long rows = (long long)((o->n_max + B - 1) / B) * B + 1;  // tiles run whole
+  p->Mw = (int)(rows + 2 * B + 2);
+  auto alloc = [&](void** ptr, size_t bytes) { return cudaMalloc(ptr, bytes) == cudaSuccess; };
+  if (!alloc((void**)&p->status, sizeof(unsigned long long)) ||
+      !alloc((void**)&p->F1, (size_t)(rows + B) * d * sizeof(double)) ||
+      !alloc((void**)&p->far1, (size_t)2 * B * 2 * d * sizeof(double)) ||
+      !alloc((void**)&p->part1, (size_t)2 * p->G * B * 2 * d * sizeof(double)) ||
+      !alloc((void**)&p->tickets, 2 * sizeof(unsigned int)) ||
+      !alloc((void**)&p->hhat1, sizeof(double)))
+    return cleanup_fail(ABM_ERR_OOM);
+  p->Gp = std::min(persistent_max_grid(sys), o->far_ctas ? o->far_ctas + 1 : p->sms);
+  if (p->Gp < 2) return cleanup_fail(ABM_ERR_UNSUPPORTED);
+  if (!alloc((void**)&p->ppartial, (size_t)kPersistRing * (p->Gp - 1) * kPersistB * 2 * d * sizeof(double)) ||
+      !alloc((void**)&p->pflags, (1 + kPersistRing) * sizeof(unsigned long long)))
+    return cleanup_fail(ABM_ERR_OOM);
+  cudaMemset(p->status, 0, sizeof(unsigned long long));
+  cudaMemset(p->tickets, 0, 2 * sizeof(unsigned int));
+  if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) return cleanup_fail(ABM_ERR_CUDA);
+  for (int i = 0; i < kEventRing; ++i) {
+    if (cudaEventCreateWithFlags(&p->ev_near[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_far[i], cudaEventDisableTiming) != cudaSuccess)
+      return cleanup_fail(ABM_ERR_CUDA);
+  }
+  if (cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup_fail(ABM_ERR_CUDA);
+  if (o->max_batch > 0) {
+    // every trajectory may sit in its own tile in the worst case of many alphas
+    p->max_tiles = (o->max_batch + kTrajPerTile - 1) / kTrajPerTile + kMaxWeightSets;
+    p->max_tiles = std::min(p->max_tiles, o->max_batch);
+    p->fb_cap = (size_t)p->max_tiles * rows * kTrajPerTile * d;
+    size_t far_units = (size_t)p->max_tiles + 2 * (size_t)p->sms + 16;
+    p->farb_cap = far_units * 2 * B * kTrajPerTile * d;
+    if (!alloc((void**)&p->Fb, p->fb_cap * sizeof(double)) ||
+        (o->prec != ABM_PREC_FP64 && !alloc((void**)&p->Fb32, p->fb_cap * sizeof(float))) ||
+        !alloc((void**)&p->farb, p->farb_cap * sizeof(double)) ||
+        !alloc((void**)&p->d_tiles, (size_t)p->max_tiles * sizeof(TileDesc)) ||
+        !alloc((void**)&p->d_h, (size_t)o->max_batch * sizeof(double)) ||
+        !alloc((void**)&p->d_N, (size_t)o->max_batch * sizeof(int)) ||
+        !alloc((void**)&p->d_hhat, (size_t)o->max_batch * sizeof(double)) ||
+        !alloc((void**)&p->d_balpha, kMaxWeightSets * sizeof(double)) ||
+        !alloc((void**)&p->d_bg, kMaxWeightSets * sizeof(double)) ||
+        !alloc((void**)&p->d_bptr, 3 * kMaxWeightSets * sizeof(double*)) ||
+        !alloc((void**)&p->d_b32ptr, 2 * kMaxWeightSets * sizeof(float*)))
+      return cleanup_fail(ABM_ERR_OOM);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return cleanup_fail(ABM_ERR_CUDA);
+  *out = p;
+  return ABM_OK;
+}
+
+abm_status abm_plan_destroy(abm_plan p) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  for (auto& w : p->wsets) {
+    cudaFree(w.b); cudaFree(w.a); cudaFree(w.c); cudaFree(w.g); cudaFree(w.b32); cudaFree(w.a32);
+  }
+  cudaFree(p->ppartial); cudaFree(p->pflags);
+  cudaFree(p->F1); cudaFree(p->far1); cudaFree(p->part1); cudaFree(p->tickets); cudaFree(p->hhat1);
+  cudaFree(p->Fb); cudaFree(p->Fb32); cudaFree(p->farb); cudaFree(p->d_tiles); cudaFree(p->d_h);
+  cudaFree(p->d_N); cudaFree(p->d_hhat); cudaFree(p->d_balpha); cudaFree(p->d_bg);
+  cudaFree(p->d_bptr); cudaFree(p->d_b32ptr); cudaFree(p->status);
+  if (p->side) cudaStreamDestroy(p->side);
+  for (int i = 0; i < kEventRing; ++i) {
+    if (p->ev_near[i]) cudaEventDestroy(p->ev_near[i]);
+    if (p->ev_far[i]) cudaEventDestroy(p->ev_far[i]);
+  }
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  delete p;
+  return ABM_OK;
+}
+
+abm_status abm_plan_sync(abm_plan p, void* stream, int64_t* where) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(st), "stream synchronize");
+  unsigned long long w = 0;
+  CK(cudaMemcpy(&w, p->status, sizeof(w), cudaMemcpyDeviceToHost), "status read");
+  if (w) CK(cudaMemset(p->status, 0, sizeof(w)), "status clear");
+  int code = (int)(w >> 60);
+  if (where) *where = (int64_t)(w & 0x0FFFFFFFFFFFFFFFull);
+  if (code == 0) return ABM_OK;
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "device reported %s at trajectory %llu step %llu",
+                code == ABM_ERR_NONFINITE ? "a non-finite value" : "a wait that ran out",
+                (w >> 32) & 0x0FFFFFFFull, w & 0xFFFFFFFFull);
+  return fail(p, (abm_status)code, buf);
+}
+
+abm_status abm_weights(abm_plan p, double alpha, int M, double* b, double* a, double* c, void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (!alpha_ok(alpha) || M < 0 || !b || !a || !c)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_weights: alpha must be in (0,1], M >= 0, arrays non-null");
+  CK(launch_weights(alpha, M, b, a, c, nullptr, (cudaStream_t)stream), "weights kernel");
+  return ABM_OK;
+}
+
+abm_status abm_far_history(abm_plan p, double alpha, const double* F, long long rows, long long cols,
+                           long long s, int B, long long k_lo, long long k_hi, double* P, double* C,
+                           void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (!alpha_ok(alpha) || !F || !P || !C || rows < 1 || (cols != 1 && cols != 3) || B != p->B ||
+      k_lo < 1 || k_hi < k_lo || k_hi > s || s >= rows || s + B > p->Mw - 2 * p->B)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_far_history: bad arguments");
+  if (p->o.prec != ABM_PREC_FP64) return fail(p, ABM_ERR_UNSUPPORTED, "abm_far_history: FP64 plans only");
+  cudaStream_t st = (cudaStream_t)stream;
+  WeightSet* w;
+  abm_status rs = get_weights(p, alpha, st, &w);
+  if (rs) return rs;
+  const int d = (int)cols;
+  std::vector<double> zero;
+  if (k_hi == k_lo) {
+    CK(cudaMemsetAsync(P, 0, sizeof(double) * B * d, st), "memset");
+    CK(cudaMemsetAsync(C, 0, sizeof(double) * B * d, st), "memset");
+    return ABM_OK;
+  }
+  long long K = k_hi - k_lo;
+  int grid = (int)std::min<long long>(p->G, (K + 63) / 64);
+  FarSingleArgs A{F, w->b, w->a, s, k_lo, k_hi, (K + grid - 1) / grid, p->part1, p->far1, p->tickets};
+  CK(launch_far_single(d, A, B, grid, st), "far kernel");
+  // de-interleave [B][2d] into P and C
+  CK(cudaMemcpy2DAsync(P, d * sizeof(double), p->far1, 2 * d * sizeof(double), d * sizeof(double), B,
+                       cudaMemcpyDeviceToDevice, st), "copy P");
+  CK(cudaMemcpy2DAsync(C, d * sizeof(double), p->far1 + d, 2 * d * sizeof(double), d * sizeof(double), B,
+                       cudaMemcpyDeviceToDevice, st), "copy C");
+  return ABM_OK;
+}
+
+abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* params, const double* y0,
+                     double* Y, double* YP, void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (!alpha_ok(alpha) || !(std::isfinite(h) && h > 0.0) || N < 1 || N > p->o.n_max || !params || !y0 || !Y)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve: need alpha in (0,1], finite h > 0, 1 <= N <= n_max, "
+                                        "non-null params/y0/Y");
+  TrajParams tp{};
+  for (int i = 0; i < p->np; ++i) {
+    if (!std::isfinite(params[i])) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve: non-finite parameter");
+    tp.p[i] = params[i];
+  }
+  for (int i = 0; i < p->d; ++i) {
+    if (!std::isfinite(y0[i])) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve: non-finite y0");
+    tp.y0[i] = y0[i];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  WeightSet* w;
+  abm_status rs = get_weights(p, alpha, st, &w);
+  if (rs) return rs;
+  // one cooperative launch: CTA 0 steps, CTAs 1..Gp-1 compute the far history
+  CK(cudaMemsetAsync(p->pflags, 0, (1 + kPersistRing) * sizeof(unsigned long long), st), "flags reset");
+  PersistArgs A{};
+  A.F = p->F1;
+  A.Y = Y;
+  A.YP = YP;
+  A.b = w->b;
+  A.a = w->a;
+  A.c = w->c;
+  A.g = w->g;
+  A.partial = p->ppartial;
+  A.flags = p->pflags;
+  A.status = p->status;
+  A.tp = tp;
+  A.alpha = alpha;
+  A.h = h;
+  A.N = N;
+  A.spin_budget = p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL;
+  A.withhold_tile = p->o.test_withhold_tile > 0 ? p->o.test_withhold_tile - 1 : -1;
+  CK(launch_persistent(p->sys, A, p->Gp, st), "persistent single-trajectory kernel");
+  return ABM_OK;
+}
+
+abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const double* h, const int* N,
+                             const double* params, const double* y0, double* Y, long long ldY, double* YP,
+                             void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: need 1 <= M <= max_batch and non-null arrays");
+  int nmax = 0;
+  for (int i = 0; i < M; ++i) {
+    if (!alpha_ok(alpha[i]) || !(std::isfinite(h[i]) && h[i] > 0.0) || N[i] < 1 || N[i] > p->o.n_max)
+      return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: trajectory " + std::to_string(i) +
+                                              " needs alpha in (0,1], finite h > 0, 1 <= N <= n_max");
+    nmax = std::max(nmax, N[i]);
+  }
+  if (ldY < (long long)nmax + 1) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: ldY < max(N)+1");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = p->B, d = p->d;
+  // ---- alpha groups ----
+  std::vector<double> ualpha;
+  for (int i = 0; i < M; ++i)
+    if (std::find(ualpha.begin(), ualpha.end(), alpha[i]) == ualpha.end()) ualpha.push_back(alpha[i]);
+  if ((int)ualpha.size() > kMaxWeightSets)
+    return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: more distinct alpha values than weight sets");
+  std::vector<WeightSet*> ws(ualpha.size());
+  for (size_t g = 0; g < ualpha.size(); ++g) {
+    abm_status rs = get_weights(p, ualpha[g], st, &ws[g]);
+    if (rs) return rs;
+  }
+  // ---- column tiles: per group, ordered by N descending, 32 trajectories each ----
+  std::vector<TileDesc> tiles;
+  for (size_t g = 0; g < ualpha.size(); ++g) {
+    std::vector<int> idx;
+    for (int i = 0; i < M; ++i)
+      if (alpha[i] == ualpha[g]) idx.push_back(i);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return N[x] > N[y]; });
+    for (size_t q = 0; q < idx.size(); q += kTrajPerTile) {
+      TileDesc t{};
+      for (int l = 0; l < kTrajPerTile; ++l) t.traj[l] = (q + l < idx.size()) ? idx[q + l] : -1;
+      t.bucket = (int)g;
+      t.n_tile = N[idx[q]];
+      tiles.push_back(t);
+    }
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const TileDesc& x, const TileDesc& y) { return x.n_tile > y.n_tile; });
+  if ((int)tiles.size() > p->max_tiles)
+    return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: too many column tiles for this plan");
+  size_t off = 0;
+  for (auto& t : tiles) {
+    t.f_off = (long long)off;
+    long long rows = (long long)((t.n_tile + B - 1) / B) * B + 1;
+    off += (size_t)rows * kTrajPerTile * d;
+  }
+  if (off > p->fb_cap) return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: history exceeds workspace");
+  const int n_tiles = (int)tiles.size();
+  int ksplit = std::max(1, std::min(16, (2 * p->sms + n_tiles - 1) / n_tiles));
+  while ((size_t)ksplit * n_tiles * 2 * B * kTrajPerTile * d > p->farb_cap && ksplit > 1) --ksplit;
+  // ---- device tables ----
+  std::vector<double> balpha(ualpha), bg(ualpha.size());
+  std::vector<const double*> bptr(3 * kMaxWeightSets, nullptr);
+  std::vector<const float*> b32ptr(2 * kMaxWeightSets, nullptr);
+  for (size_t g = 0; g < ualpha.size(); ++g) {
+    bptr[g] = ws[g]->b;
+    bptr[kMaxWeightSets + g] = ws[g]->a;
+    bptr[2 * kMaxWeightSets + g] = ws[g]->c;
+    b32ptr[g] = ws[g]->b32;
+    b32ptr[kMaxWeightSets + g] = ws[g]->a32;
+    CK(cudaMemcpyAsync(p->d_bg + g, ws[g]->g, sizeof(double), cudaMemcpyDeviceToDevice, st), "g copy");
+  }
+  CK(cudaMemcpyAsync(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st), "tiles");
+  CK(cudaMemcpyAsync(p->d_h, h, M * sizeof(double), cudaMemcpyHostToDevice, st), "h");
+  CK(cudaMemcpyAsync(p->d_N, N, M * sizeof(int), cudaMemcpyHostToDevice, st), "N");
+  CK(cudaMemcpyAsync(p->d_balpha, balpha.data(), balpha.size() * sizeof(double), cudaMemcpyHostToDevice, st), "alpha");
+  CK(cudaMemcpyAsync(p->d_bptr, bptr.data(), bptr.size() * sizeof(double*), cudaMemcpyHostToDevice, st), "ptrs");
+  CK(cudaMemcpyAsync(p->d_b32ptr, b32ptr.data(), b32ptr.size() * sizeof(float*), cudaMemcpyHostToDevice, st), "ptrs");
+  BatchArgs A{};
+  A.tiles = p->d_tiles;
+  A.n_tiles = n_tiles;
+  A.B = B;
+  A.ksplit = ksplit;
+  A.bucket_alpha = p->d_balpha;
+  A.bucket_b = p->d_bptr;
+  A.bucket_a = p->d_bptr + kMaxWeightSets;
+  A.bucket_c = p->d_bptr + 2 * kMaxWeightSets;
+  A.bucket_b32 = p->d_b32ptr;
+  A.bucket_a32 = p->d_b32ptr + kMaxWeightSets;
+  A.bucket_g = p->d_bg;
+  A.h = p->d_h;
+  A.N = p->d_N;
+  A.params = params;
+  A.y0 = y0;
+  A.hhat = p->d_hhat;
+  A.F = p->Fb;
+  A.F32 = (p->o.prec == ABM_PREC_FP64) ? nullptr : p->Fb32;
+  A.far = p->farb;
+  A.Y = Y;
+  A.YP = YP;
+  A.ldY = ldY;
+  A.status = p->status;
+  CK(launch_batched_setup(p->sys, A, n_tiles, st), "setup kernel");
+  const int ntime = (nmax + B - 1) / B;
+  int n_active = n_tiles;
+  for (int j = 0; j < ntime; ++j) {
+    const long long s = (long long)j * B;
+    while (n_active > 0 && tiles[n_active - 1].n_tile <= s) --n_active;
+    if (n_active == 0) break;
+    if (s > 1) CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
+    CK(launch_batched_near(p->sys, A, n_active, s, B, st), "near kernel");
+  }
+  return ABM_OK;
+}
+
+abm_status abm_adjoint(abm_plan p, int, const double*, const double*, const int*, const double*, const double*,
+                       const double*, const double*, long long, const double*, double*, double*, void*) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  return fail(p, ABM_ERR_UNSUPPORTED, "abm_adjoint: not built yet");
+}
+
+}  // extern "C"

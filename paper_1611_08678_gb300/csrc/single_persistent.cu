@@ -1,0 +1,345 @@
+// Single-trajectory path (abm_solve) as one cooperative persistent kernel,
+// FP64 throughout.  Time tiles of PB = 32 target steps.
+//
+// CTA 0 (near role) runs the sequential PECE steps of Sec. 2:
+//   warps 0..D-1 : the chain, one state component per warp (component c on
+//                  warp c, so the components of f evaluate on different
+//                  SM sub-partitions): y^P_{n+1}, f(t_{n+1}, y^P), y_{n+1},
+//                  f(t_{n+1}, y_{n+1}) (eq. (2) predictor and the corrector)
+//   warp 3       : the scatter - when f_n is final it adds its contribution
+//                  w_{m-n} f_n to every later target m of this tile and of
+//                  the next tile (lane = target), so no per-step reduction is
+//                  needed; the chain only adds the lag-0 term itself
+// CTAs 1..G-1 (far role) compute, for tile j (targets [jB, jB+B)), the sums
+// over history rows [1, (j-1)B) - rows that were final before tile j-1
+// started, so far(j) overlaps the near steps of tile j-1.  CTA 0 adds the G-1
+// partials in a fixed order (deterministic), plus the k = 0 terms
+// b_n f_0, c_n f_0.  Rows [(j-1)B, jB) reach tile j through the scatter.
+// This is the per-tile form of the paper's partial sums over earlier blocks
+// gathered by the block owner (Sec. 3, Fig. 2).
+//
+// Synchronisation: CTA 0 publishes rows_done after each tile; far CTAs
+// publish one count per tile slot.  Every wait is a bounded spin (clock64
+// budget) that also gives up when another CTA has reported an error, so the
+// kernel always terminates; a wait that runs out sets ABM_ERR_TIMEOUT.
+#include <cuda/atomic>
+
+#include "common.cuh"
+#include "single.cuh"
+#include "systems.cuh"
+
+namespace abm {
+
+namespace {
+
+constexpr int PB = kPersistB;  // time-tile length
+constexpr int PR = 4;          // ring of far slots
+constexpr int PT = 256;        // threads per CTA
+
+using dev_atomic = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
+
+__device__ bool spin_geq(unsigned long long* flag, unsigned long long target, unsigned long long* status,
+                         long long budget, int where, long long detail) {
+  dev_atomic f(*flag), st(*status);
+  const long long t0 = clock64();
+  while (f.load(cuda::memory_order_acquire) < target) {
+    if (st.load(cuda::memory_order_relaxed) != 0ull) return false;
+    if (clock64() - t0 > budget) {
+      report_status(status, ABM_ERR_TIMEOUT, where, detail);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void named_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+}  // namespace
+
+// Sums over history rows [c0, c1) for targets s..s+B-1 of
+//   b_{s+i-k} F[k][c] and a_{s+i-k} F[k][c];  writes B x 2D values to out.
+// NT threads: each owns R consecutive targets over a contiguous sub-range of
+// rows, the Toeplitz weights kept as a sliding register window.  F is read
+// through L2 (ld.global.cg): rows next to the ones read may be written by
+// another SM later in the same launch.
+template <int D, int B, int R, int NT>
+__device__ void far_chunk(const double* __restrict__ F, const double* __restrict__ b,
+                          const double* __restrict__ a, long long s, long long c0, long long c1,
+                          double* red, double* out) {
+  constexpr int RG = B / R, KL = NT / RG, V = 2 * D;
+  static_assert(RG * KL == NT, "thread layout");
+  const int tid = threadIdx.x, rg = tid % RG, kl = tid / RG, i0 = rg * R;
+  const long long len = c1 > c0 ? c1 - c0 : 0;
+  const long long sub = (len + KL - 1) / KL;
+  const long long kb = c0 + kl * sub, ke = min(c1, kb + sub);
+  double accP[R][D], accC[R][D];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) accP[r][c] = accC[r][c] = 0.0;
+  if (kb < ke) {
+    double wb[R], wa[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      wb[r] = __ldg(b + (s + i0 + r - kb));
+      wa[r] = __ldg(a + (s + i0 + r - kb));
+    }
+    for (long long k = kb; k < ke; ++k) {
+      double f[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) f[c] = __ldcg(F + k * D + c);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          accP[r][c] = fma(wb[r], f[c], accP[r][c]);
+          accC[r][c] = fma(wa[r], f[c], accC[r][c]);
+        }
+#pragma unroll
+      for (int r = R - 1; r > 0; --r) { wb[r] = wb[r - 1]; wa[r] = wa[r - 1]; }
+      if (k + 1 < ke) {
+        wb[0] = __ldg(b + (s + i0 - (k + 1)));
+        wa[0] = __ldg(a + (s + i0 - (k + 1)));
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      red[kl * (B * V) + (i0 + r) * V + c] = accP[r][c];
+      red[kl * (B * V) + (i0 + r) * V + D + c] = accC[r][c];
+    }
+  __syncthreads();
+  for (int idx = tid; idx < B * V; idx += NT) {
+    double sum = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < KL; ++q) sum += red[q * (B * V) + idx];
+    out[idx] = sum;
+  }
+  __syncthreads();
+}
+
+template <int SYS>
+__global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A) {
+  using S = Sys<SYS>;
+  constexpr int D = S::D, V = 2 * D;
+  extern __shared__ __align__(16) double dyn[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int W = gridDim.x - 1;  // far CTAs
+  const int N = A.N;
+  const int ntiles = (N + PB - 1) / PB;
+  unsigned long long* rows_done = A.flags;
+  unsigned long long* far_count = A.flags + 1;  // [PR]
+  __shared__ int ok_s;
+
+  if (blockIdx.x > 0) {
+    // ------------------------------ far role ------------------------------
+    const int w = blockIdx.x - 1;
+    for (int j = 2; j < ntiles; ++j) {
+      const long long s = (long long)j * PB, e = (long long)(j - 1) * PB;
+      if (tid == 0) ok_s = spin_geq(rows_done, (unsigned long long)e, A.status, A.spin_budget, 1, j);
+      __syncthreads();
+      if (!ok_s) return;
+      const long long K = e - 1, chunk = (K + W - 1) / W;
+      const long long c0 = 1 + (long long)w * chunk, c1 = min(e, c0 + chunk);
+      far_chunk<D, PB, 4, PT>(A.F, A.b, A.a, s, c0, c1, dyn,
+                              A.partial + ((size_t)(j % PR) * W + w) * (PB * V));
+      __threadfence();
+      __syncthreads();
+      if (tid == 0 && j != A.withhold_tile) atomicAdd(far_count + (j % PR), 1ull);
+    }
+    return;
+  }
+
+  // -------------------------------- near role --------------------------------
+  double* farv = dyn;                    // [PB * V]
+  double* wsb = farv + PB * V;           // lags 0..2PB
+  double* wsa = wsb + (2 * PB + 1);
+  __shared__ double Fs[4][kMaxD];        // ring of the last f rows
+  __shared__ double accn[2][8];          // sums handed from the scatter warp to the chain
+  __shared__ double ysh[kMaxD], ysh2[kMaxD], F0s[kMaxD], consts[2];
+
+  const double* p = A.tp.p;
+  for (int m = tid; m <= 2 * PB; m += PT) { wsb[m] = A.b[m]; wsa[m] = A.a[m]; }
+  if (tid == 0) {
+    consts[0] = pow(A.h, A.alpha);
+    consts[1] = *A.g;
+  }
+  if (warp < D && lane == 0) {
+    const int c = warp;
+    double y0v[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) y0v[q] = A.tp.y0[q];
+    const double f0 = S::fc(c, p, A.alpha, 0.0, y0v);
+    F0s[c] = f0;
+    Fs[0][c] = f0;
+    A.F[c] = f0;
+    A.Y[c] = A.tp.y0[c];
+    if (A.YP) A.YP[c] = A.tp.y0[c];
+  }
+  __syncthreads();
+  const double hh = consts[0], g = consts[1], h = A.h;
+
+  // scatter-warp registers: sums for targets of this tile (cur) and the next
+  double sPc[D], sCc[D], sPn[D], sCn[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) sPc[q] = sCc[q] = sPn[q] = sCn[q] = 0.0;
+
+  for (int j = 0; j < ntiles; ++j) {
+    const long long s = (long long)j * PB;
+    const int nb = (int)min((long long)PB, (long long)N - s);
+    // ---- far sums of this tile: fixed-order sum of the W partials ----
+    if (j >= 2) {
+      if (tid == 0) {
+        const unsigned long long target = (unsigned long long)W * (unsigned long long)((j - 2) / PR + 1);
+        ok_s = spin_geq(far_count + (j % PR), target, A.status, A.spin_budget, 0, j);
+      }
+      __syncthreads();
+      if (!ok_s) return;
+      const double* base = A.partial + (size_t)(j % PR) * W * (PB * V);
+      for (int idx = tid; idx < PB * V; idx += PT) {
+        double sum = 0.0;
+        for (int q = 0; q < W; ++q) sum += __ldcg(base + (size_t)q * (PB * V) + idx);
+        farv[idx] = sum;
+      }
+    } else {
+      for (int idx = tid; idx < PB * V; idx += PT) farv[idx] = 0.0;
+    }
+    __syncthreads();
+    // ---- scatter prologue: hand over the next-tile sums, add far and k = 0 terms ----
+    if (warp == 3) {
+      const long long m = s + lane;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        sPc[q] = sPn[q]; sCc[q] = sCn[q];
+        sPn[q] = 0.0; sCn[q] = 0.0;
+      }
+      if (lane < nb) {
+        const double bm = A.b[m], cm = A.c[m];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          sPc[q] += fma(bm, F0s[q], farv[lane * V + q]);
+          sCc[q] += fma(cm, F0s[q], farv[lane * V + D + q]);
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) { accn[0][q] = sPc[q]; accn[0][D + q] = sCc[q]; }
+      }
+    }
+    __syncthreads();
+    // ---- the nb sequential steps ----
+    if (warp < 4) {
+      for (int i = 0; i < nb; ++i) {
+        const long long n = s + i;
+        const int par = i & 1;
+        if (warp < D) {
+          const int c = warp;
+          const double t1 = (double)(n + 1) * h;
+          double y0c = A.tp.y0[0];
+#pragma unroll
+          for (int q = 1; q < D; ++q) y0c = (c == q) ? A.tp.y0[q] : y0c;
+          double v = 0.0;
+          if (lane < 2) {
+            v = accn[par][lane == 0 ? c : D + c];
+            if (n >= 1) v = fma(lane == 0 ? wsb[0] : wsa[0], Fs[n & 3][c], v);
+          }
+          const double vc = __shfl_sync(0xffffffffu, v, 1);
+          const double yp = fma(hh, v, y0c);
+          if (lane == 0) ysh[c] = yp;
+          named_bar(2, 32 * D);
+          double ypv[D];
+#pragma unroll
+          for (int q = 0; q < D; ++q) ypv[q] = ysh[q];
+          const double fp = S::fc(c, p, A.alpha, t1, ypv);
+          const double y = fma(hh, fma(g, fp, vc), y0c);
+          if (lane == 0) ysh2[c] = y;
+          named_bar(2, 32 * D);
+          double yv[D];
+#pragma unroll
+          for (int q = 0; q < D; ++q) yv[q] = ysh2[q];
+          const double fy = S::fc(c, p, A.alpha, t1, yv);
+          if (lane == 0) {
+            Fs[(n + 1) & 3][c] = fy;
+            A.F[(n + 1) * D + c] = fy;
+            A.Y[(n + 1) * D + c] = y;
+            if (A.YP) A.YP[(n + 1) * D + c] = yp;  // lane 0 of warp c holds component c
+            if (!isfinite(y) || !isfinite(fy)) report_status(A.status, ABM_ERR_NONFINITE, 0, n + 1);
+          }
+        } else if (warp == 3) {
+          if (n >= 1) {
+            double fn[D];
+#pragma unroll
+            for (int q = 0; q < D; ++q) fn[q] = Fs[n & 3][q];
+            const long long lagc = s + lane - n;       // target s+lane of this tile
+            if (lagc > 0) {
+              const double wb = wsb[lagc], wa = wsa[lagc];
+#pragma unroll
+              for (int q = 0; q < D; ++q) { sPc[q] = fma(wb, fn[q], sPc[q]); sCc[q] = fma(wa, fn[q], sCc[q]); }
+            }
+            const long long lagn = s + PB + lane - n;  // target s+PB+lane of the next tile, >= 1
+            const double wb = wsb[lagn], wa = wsa[lagn];
+#pragma unroll
+            for (int q = 0; q < D; ++q) { sPn[q] = fma(wb, fn[q], sPn[q]); sCn[q] = fma(wa, fn[q], sCn[q]); }
+          }
+          if (i + 1 < nb && lane == i + 1) {
+#pragma unroll
+            for (int q = 0; q < D; ++q) { accn[par ^ 1][q] = sPc[q]; accn[par ^ 1][D + q] = sCc[q]; }
+          }
+        }
+        named_bar(1, 128);
+      }
+    }
+    // ---- publish: rows 0..s+nb are final ----
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      dev_atomic rd(*rows_done);
+      rd.store((unsigned long long)(s + nb + 1), cuda::memory_order_release);
+    }
+    if (tid == 0) {
+      dev_atomic st(*A.status);
+      ok_s = st.load(cuda::memory_order_relaxed) == 0ull;  // any reported error ends the solve
+    }
+    __syncthreads();
+    if (!ok_s) return;
+  }
+}
+
+size_t persistent_smem_bytes() { return 116 * 1024; }
+
+template <int SYS>
+cudaError_t launch_persistent_t(const PersistArgs& A, int grid, cudaStream_t st) {
+  auto fn = single_persistent_kernel<SYS>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)persistent_smem_bytes());
+  if (e != cudaSuccess) return e;
+  PersistArgs a = A;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((void*)fn, dim3(grid), dim3(PT), args, persistent_smem_bytes(), st);
+}
+
+cudaError_t launch_persistent(int sys, const PersistArgs& A, int grid, cudaStream_t st) {
+  cudaError_t err = cudaErrorInvalidValue;
+  ABM_DISPATCH_SYSTEM(sys, err = launch_persistent_t<SYS>(A, grid, st));
+  return err;
+}
+
+int persistent_max_grid(int sys) {
+  int blocks = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  ABM_DISPATCH_SYSTEM(sys, {
+    cudaFuncSetAttribute(single_persistent_kernel<SYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)persistent_smem_bytes());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, single_persistent_kernel<SYS>, PT,
+                                                  persistent_smem_bytes());
+  });
+  return blocks * sms;
+}
+
+}  // namespace abm

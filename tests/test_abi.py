@@ -1,0 +1,75 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function include/abm.h declares; host-side argument checks that run before
+any CUDA call reject bad plans.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1611_08678_gb300 import abm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(abm_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = abm.load()
+    declared = _declared_functions()
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(abm.EXPORTS) <= declared
+
+
+def test_system_catalogue_dims():
+    lib = abm.load()
+    assert [lib.abm_system_dim(i) for i in range(6)] == [1, 1, 3, 3, 3, 3]
+    assert [lib.abm_system_nparams(i) for i in range(6)] == [3, 9, 3, 3, 3, 3]
+    assert lib.abm_system_dim(17) == -1
+
+
+def test_plan_create_rejects_bad_options_before_any_cuda_call():
+    lib = abm.load()
+    h = ctypes.c_void_p()
+    o = abm.PlanOpts()
+    lib.abm_plan_opts_default(ctypes.byref(o))
+    o.n_max = 0
+    assert lib.abm_plan_create(ctypes.byref(h), 2, ctypes.byref(o)) == 1
+    o.n_max = 10
+    o.reserved[3] = 1
+    assert lib.abm_plan_create(ctypes.byref(h), 2, ctypes.byref(o)) == 1
+    o.reserved[3] = 0
+    o.max_batch = -1
+    assert lib.abm_plan_create(ctypes.byref(h), 2, ctypes.byref(o)) == 1
+    o.max_batch = 0
+    assert lib.abm_plan_create(ctypes.byref(h), 99, ctypes.byref(o)) == 1
+    o.tile_B = 48
+    assert lib.abm_plan_create(ctypes.byref(h), 2, ctypes.byref(o)) == 6
+    assert not h.value
+
+
+def test_product_path_has_no_oracle_or_cpu_fallback():
+    """The package never imports the oracle, and the binding raises without a GPU."""
+    pkg = os.path.join(ROOT, "paper_1611_08678_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in text and "from oracle" not in text, fn
+                assert "abm_oracle" not in text, fn
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError):
+            abm.Plan("lorenz", n_max=10)

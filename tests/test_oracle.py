@@ -394,3 +394,24 @@ def test_mutants_are_caught(name, tmp_path):
 
 def test_unmutated_oracle_passes_compact_pins():
     assert _pins_pass()
+
+
+def test_chen_pointwise_window_is_set_by_conditioning():
+    """The Chen workload (a=35, b=3, c=28, alpha=0.9, h=0.001) amplifies a
+    relative perturbation of 1e-16 in y0 beyond 1e-11 before t = 5, in the
+    oracle alone; any two FP64 implementations that round differently can
+    only agree to 1e-11 pointwise over a shorter window.  t <= 3 keeps the
+    amplified difference below 1e-12, so the GPU parity window for Chen is
+    t <= 3 (statistics beyond).  Lorenz at alpha = 0.98, h = 0.01 stays
+    well conditioned up to t = 5."""
+    p = [35.0, 3.0, 28.0]
+    y0 = np.array([-9.0, -5.0, 14.0])
+    Y, _ = oracle.solve("chen", 0.9, 0.001, 5000, p, y0)
+    Y2, _ = oracle.solve("chen", 0.9, 0.001, 5000, p, y0 * (1 + 1e-16 * np.array([1.0, -1.0, 1.0])))
+    from tests._metrics import rel_err
+    assert rel_err(Y2, Y) > 1e-11
+    assert rel_err(Y2[:3001], Y[:3001]) < 1e-12
+    L, _ = oracle.solve("lorenz", 0.98, 0.01, 500, [10.0, 28.0, 8 / 3], [0.1, 0.1, 0.1])
+    L2, _ = oracle.solve("lorenz", 0.98, 0.01, 500, [10.0, 28.0, 8 / 3],
+                         np.array([0.1, 0.1, 0.1]) * (1 + 1e-16 * np.array([1.0, -1.0, 1.0])))
+    assert rel_err(L2, L) < 1e-13
