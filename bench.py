@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the fractional ABM history convolution on GB300.
+
+Default workload: the fractional Chen system as one long trajectory
+(a=35, b=3, c=28, alpha=0.9, y0=(-9,-5,14), h=0.001, N=2^18, d=3), plain FP64
+path (abm_solve: one cooperative persistent launch per solve).  One "step" =
+one whole solve.  Metric: trajectory-steps/s (history MAC/s reported beside).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload chen_single|lorenz_single|rossler_batched|financial_batched]
+
+Multi-GPU (torchrun, one rank per GPU): single-trajectory workloads run one
+replica per rank (the path does not shard); batched workloads shard the
+trajectories across ranks.  Both are weak scaling with no data-path
+collective; the timing is the max over ranks.
+
+The oracle (plain FP64 CPU implementation under oracle/) is executed here only
+for the cpu_baseline leg and for --impl reference.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Nominal FP64 rate of GB300 (profiling recipe: 1.25 TFLOP/s) - the peak of
+# the ALU-bound FP64 path.  The measured HBM / bf16 peaks are read from
+# MEASURED_PEAKS.json for the HBM/tensor-bound kernels.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop x max clock
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture (see
+# profiles/); None when the kernel changed since the counters were taken.
+NCU_TRAFFIC = {
+    "chen_single": 7071488 + 95232,  # profiles/single_persistent_kernel_chen_N262144.md
+}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="chen_single",
+                    choices=["chen_single", "lorenz_single", "rossler_batched", "financial_batched"])
+    ap.add_argument("--prec", default=None, help="far-history precision of batched workloads")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mib", type=int, default=256)
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+def workload(name):
+    from paper_1611_08678_gb300 import workloads as wl
+    if name == "chen_single":
+        return wl.chen_single(), "fp64"
+    if name == "lorenz_single":
+        return wl.lorenz_single(), "fp64"
+    if name == "rossler_batched":
+        return wl.rossler_batched(), "fp32"
+    if name == "financial_batched":
+        return wl.financial_batched(), "fp32"
+    raise ValueError(name)
+
+
+def is_single(name):
+    return name.endswith("_single")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        loaded = [x for x in sm if x > 0.5 * max(sm)] if sm else []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def rel_err(y, ref):
+    """max_n |y_n - ref_n|_inf / max(|ref_n|_inf, 1e-3 max_m |ref_m|_inf)"""
+    import numpy as np
+    nrm = np.abs(ref).max(axis=1)
+    den = np.maximum(nrm, 1e-3 * nrm.max())
+    return float(np.max(np.abs(y - ref).max(axis=1) / den))
+
+
+def oracle_single_rate(w, n_sample):
+    """Oracle (CPU, one thread) on the first n_sample steps of a single
+    trajectory; returns (seconds, Y)."""
+    import oracle
+    t0 = time.perf_counter()
+    Y, _ = oracle.solve(w.system, float(w.alpha[0]), float(w.h[0]), n_sample, w.params[0], w.y0[0])
+    return time.perf_counter() - t0, Y
+
+
+def single_cpu_baseline(w, n_sample):
+    """Oracle MAC rate on the sample, scaled to full-workload trajectory-steps/s."""
+    N, d = int(w.N[0]), w.d
+    sec, Y = oracle_single_rate(w, n_sample)
+    mac_rate = n_sample * (n_sample + 1) * d / sec
+    steps_per_s = mac_rate / ((N + 1) * d)  # a full solve costs (N+1) d MACs per step on average
+    return {"value": steps_per_s, "unit": "trajectory-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n_sample} steps of the {N}-step trajectory on 1 host thread "
+                      f"({sec:.2f} s), scaled by history MACs to the full solve",
+            "history_mac_per_s": mac_rate}, Y
+
+
+def bench_single(args, name, w, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1611_08678_gb300 import abm
+    N, d = int(w.N[0]), w.d
+    alpha, h = float(w.alpha[0]), float(w.h[0])
+    plan = abm.Plan(w.system, n_max=N)
+    Y = torch.empty(N + 1, d, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(args.flush_mib * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        plan.solve(alpha, h, N, w.params[0], w.y0[0], Y=Y, sync=False, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    plan.sync(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 flush between timed steps (outside the event pair)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    plan.sync(stream)  # raises on any device-side error
+    per_step = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    total = sum(per_step)
+    t = torch.tensor([total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_max = float(t.item())
+    steps_total = args.steps * N * world
+    value = steps_total / total_max
+    macs = N * (N + 1) * d
+    mean_launch = total / args.steps
+    achieved = 2.0 * macs / mean_launch / 1e12
+
+    # e2e: the public call with host buffers: params / y0 from pinned host
+    # memory (by value through the ABI), the solution copied back to pinned
+    # host memory, every step.
+    Yh = torch.empty(N + 1, d, dtype=torch.float64, pin_memory=True)
+    p_host = torch.tensor(w.params[0], dtype=torch.float64).pin_memory()
+    y0_host = torch.tensor(w.y0[0], dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, args.steps // 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        plan.solve(alpha, h, N, p_host.numpy(), y0_host.numpy(), Y=Y, sync=False, stream=stream)
+        Yh.copy_(Y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.sync(stream)
+    e2e_sec = e0.elapsed_time(e1) / 1e3
+    e2e = {"value": e2e_steps * N * world / e2e_sec, "unit": "trajectory-steps/s",
+           "h2d_bytes_per_step": int((w.params.shape[1] + d) * 8), "d2h_bytes_per_step": int((N + 1) * d * 8)}
+
+    out = {
+        "metric": "trajectory-steps/s (plain FP64 path; history MAC/s beside)",
+        "value": value, "unit": "trajectory-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_max / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": name, "system": w.system, "alpha": alpha, "h": h, "N": N, "d": d,
+                   "trajectories_per_gpu": 1, "parallelism": f"replicas{world}",
+                   "l2": f"flushed between timed steps ({args.flush_mib} MiB write)",
+                   "path": "abm_solve: one cooperative persistent launch per solve"},
+        "history_mac_per_s": macs * args.steps * world / total_max,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(name),
+                     "kernel": "single_persistent_kernel", "flops_per_launch": 2.0 * macs,
+                     "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe)"},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        n_sample = min(N, 1 << 15)
+        cb, Yo = single_cpu_baseline(w, n_sample)
+        out["cpu_baseline"] = cb
+        # stated error of this run against the oracle, over its pointwise window
+        t_win = 3.0 if w.system == "chen" else 5.0
+        nwin = min(n_sample, int(round(t_win / h)))
+        out["max_rel_err_vs_oracle"] = rel_err(Y[: nwin + 1].cpu().numpy(), Yo[: nwin + 1])
+        out["error_window"] = f"t <= {t_win}"
+    return out
+
+
+def bench_reference(args, name, w, world, rank):
+    """The oracle, as it stands, on the host cores: each step a bounded sample."""
+    if rank != 0:
+        return None
+    if not is_single(name):
+        return {"impl": "reference", "unavailable": "reference arm implemented for single-trajectory workloads"}
+    N, d = int(w.N[0]), w.d
+    n_sample = min(N, 1 << 14)
+    rates = []
+    for k in range(args.warmup + args.steps):
+        sec, _ = oracle_single_rate(w, n_sample)
+        if k >= args.warmup:
+            rates.append(n_sample * (n_sample + 1) * d / sec)
+    mac_rate = statistics.mean(rates)
+    value = mac_rate / ((N + 1) * d)
+    return {"impl": "reference", "metric": "trajectory-steps/s (plain FP64 path; history MAC/s beside)",
+            "value": value, "unit": "trajectory-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": n_sample * (n_sample + 1) * d / mac_rate * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": name, "system": w.system, "N": N, "d": d},
+            "history_mac_per_s": mac_rate,
+            "cpu_baseline": {"value": value, "unit": "trajectory-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n_sample} steps per step, 1 host thread, scaled by history "
+                                       f"MACs to the {N}-step solve"},
+            "e2e": {"value": value, "unit": "trajectory-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    world, rank, local = dist_env()
+    w, _ = workload(args.workload)
+    if args.impl == "reference":
+        out = bench_reference(args, args.workload, w, world, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    if is_single(args.workload):
+        out = bench_single(args, args.workload, w, world, rank, local)
+    else:
+        raise SystemExit("batched workloads: see bench_batched (not in this revision)")
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -26,3 +26,25 @@ def stats_rel_diff(y, ref):
     a, b = stats(y), stats(ref)
     scale = np.maximum(np.abs(b), 1e-12)
     return float(np.max(np.abs(a - b) / scale))
+
+
+def chaos_stats_ratio(y, ref, refs_perturbed):
+    """Statistics beyond the pointwise window of a chaotic run.
+
+    Per component, min, max, mean and variance of y are compared with the
+    reference run's.  The allowed difference is twice the largest difference
+    between the reference and its own re-runs from initial values perturbed at
+    the rounding level (the spread the flow itself creates), and at least 1e-3
+    of the component's scale (range for min/max, standard deviation for the
+    mean, variance for the variance).  Returns max(diff / allowed): <= 1 passes.
+    """
+    s_ref = stats(ref)
+    spread = np.zeros_like(s_ref)
+    for rp in refs_perturbed:
+        spread = np.maximum(spread, np.abs(stats(rp) - s_ref))
+    ref = np.asarray(ref, dtype=np.float64)
+    rng = ref.max(axis=0) - ref.min(axis=0)
+    sd = ref.std(axis=0)
+    scale = np.stack([rng, rng, sd, ref.var(axis=0)])
+    allowed = np.maximum(2.0 * spread, 1e-3 * scale)
+    return float(np.max(np.abs(stats(y) - s_ref) / allowed))

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1611_08678_gb300 import workloads
-from tests._metrics import rel_err, stats_rel_diff
+from tests._metrics import chaos_stats_ratio, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -113,9 +113,11 @@ def test_single_lorenz_config(abm):
     n5 = int(round(5.0 / w.h[0]))
     assert rel_err(Y[: n5 + 1], Yo[: n5 + 1]) <= 1e-11
     assert np.all(np.isfinite(Y))
-    d = stats_rel_diff(Y[n5:], Yo[n5:])
-    print(f"lorenz stats rel diff beyond t=5: {d:.2e}")
-    assert d <= 5e-2
+    pert = [oracle.solve("lorenz", w.alpha[0], w.h[0], int(w.N[0]), w.params[0], w.y0[0] * (1 + 1e-15 * np.array(u)))[0]
+            for u in ((1, -1, 1), (-1, 1, 1), (1, 1, -1))]
+    r = chaos_stats_ratio(Y[n5:], Yo[n5:], [q[n5:] for q in pert])
+    print(f"lorenz statistics beyond t=5: ratio to allowed {r:.2f}")
+    assert r <= 1.0
 
 
 def test_single_chen_prefix_at_full_size(abm):
@@ -134,9 +136,11 @@ def test_single_chen_prefix_at_full_size(abm):
     assert rel_err(Y[: n3 + 1], Yo[: n3 + 1]) <= 1e-11
     assert np.all(np.isfinite(Y))
     assert np.abs(Y).max() < 200.0  # stays on the attractor
-    d = stats_rel_diff(Y[n3:Np + 1], Yo[n3:])
-    print(f"chen stats rel diff t in (3, 32.8]: {d:.2e}")
-    assert d <= 5e-2
+    pert = [oracle.solve("chen", w.alpha[0], w.h[0], Np, w.params[0], w.y0[0] * (1 + 1e-15 * np.array(u)))[0]
+            for u in ((1, -1, 1), (-1, 1, 1), (1, 1, -1))]
+    r = chaos_stats_ratio(Y[n3:Np + 1], Yo[n3:], [q[n3:] for q in pert])
+    print(f"chen statistics t in (3, 32.8]: ratio to allowed {r:.2f}")
+    assert r <= 1.0
 
 
 def test_single_tail_tiles_and_lookahead(abm):
