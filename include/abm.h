@@ -178,6 +178,38 @@ abm_status abm_far_history(abm_plan p, double alpha, const double* F, long long 
                            long long cols, long long s, int B, long long k_lo, long long k_hi,
                            double* P, double* C, void* stream);
 
+/* abm_solve_noalloc - the single-trajectory solve (abm_solve) for callers
+ * that must not allocate device memory: code whose device memory is budgeted
+ * up front by a host framework or memory pool, real-time or embedded callers
+ * that forbid allocation after start-up, and plug-ins that run inside another
+ * process's CUDA context.  The paper has no counterpart; it exists for those
+ * callers only.
+ *
+ * No plan is needed and nothing is allocated: the call makes no cudaMalloc,
+ * cudaFree or other allocating call.  Its scratch (the f history, the
+ * weights, the far-history partial sums, the wait flags and the status word)
+ * lives in one static device array of about 3.2 MB compiled into this
+ * library, which every GPU that loads the library holds until the process
+ * exits.  That fixes the largest problem: 1 <= N <= 32768 (d <= 3); larger N
+ * returns ABM_ERR_INVALID_ARG with a message saying so.
+ *
+ * Arguments as abm_solve (sys instead of a plan; params and y0 host arrays,
+ * Y and YP device arrays of (N+1)*d doubles owned by the caller, YP may be
+ * NULL), plus errbuf/errbuf_len (may be NULL/0): a message for any failure,
+ * the empty string on success.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  The call is synchronous: it waits for `stream` and returns the
+ * device status (ABM_ERR_NONFINITE, ABM_ERR_TIMEOUT) itself.  All calls share
+ * the one array, which keeps the previous call's contents (each call clears
+ * what must start at zero), so calls that overlap on the GPU - from several
+ * host threads or on several streams of one device at once - race and give
+ * wrong results; serialise them. */
+abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, int N, const double* params,
+                             const double* y0, double* Y, double* YP, void* stream, char* errbuf,
+                             size_t errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ STATUS = {0: "ABM_OK", 1: "ABM_ERR_INVALID_ARG", 2: "ABM_ERR_CUDA", 3: "ABM_ERR_
 # Every symbol include/abm.h declares (checked by the CPU test suite).
 EXPORTS = ["abm_plan_opts_default", "abm_system_dim", "abm_system_nparams", "abm_plan_create",
            "abm_plan_destroy", "abm_plan_sync", "abm_last_error", "abm_weights", "abm_solve",
-           "abm_solve_batched", "abm_adjoint", "abm_far_history"]
+           "abm_solve_batched", "abm_adjoint", "abm_far_history", "abm_solve_noalloc"]
 
 
 class AbmError(RuntimeError):
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
         lib.abm_solve_batched.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_adjoint.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp, _vp, _vp]
         lib.abm_far_history.argtypes = [_vp, D, _vp, LL, LL, LL, I, LL, LL, _vp, _vp, _vp]
+        lib.abm_solve_noalloc.argtypes = [I, D, D, I, _dp, _dp, _vp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
         for name in EXPORTS:
             if name not in ("abm_plan_opts_default", "abm_last_error", "abm_system_dim", "abm_system_nparams"):
                 getattr(lib, name).restype = I
@@ -227,3 +228,18 @@ class Plan:
         if sync:
             self.sync(stream)
         return dp, dy0
+
+
+def solve_noalloc(system: str, alpha, h, N, params, y0, Y, YP=None, stream=None):
+    """abm_solve_noalloc: single-trajectory solve whose scratch is the
+    library's static device array (no allocation).  Y (and YP) are
+    caller-provided CUDA tensors of shape (N+1, d).  Synchronous."""
+    lib = load()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    buf = ctypes.create_string_buffer(256)
+    st = lib.abm_solve_noalloc(SYSTEMS[system], float(alpha), float(h), int(N), p.ctypes.data_as(_dp),
+                               y.ctypes.data_as(_dp), _dptr(Y), _dptr(YP), _stream_ptr(stream), buf, 256)
+    if st != 0:
+        raise AbmError(st, buf.value.decode())
+    return Y

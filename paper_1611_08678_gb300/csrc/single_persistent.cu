@@ -24,6 +24,11 @@
 // kernel always terminates; a wait that runs out sets ABM_ERR_TIMEOUT.
 #include <cuda/atomic>
 
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
 #include "common.cuh"
 #include "single.cuh"
 #include "systems.cuh"
@@ -343,3 +348,147 @@ int persistent_max_grid(int sys) {
 }
 
 }  // namespace abm
+
+// ============================================================================
+// abm_solve_noalloc: the single-trajectory solve above for callers that may
+// not allocate device memory.  Its scratch (f history, weights, far partials,
+// flags, status) lives in one file-scope device array of fixed size that every
+// GPU loading this library keeps until the process exits.
+// ============================================================================
+namespace abm {
+cudaError_t launch_weights(double alpha, int M, double* b, double* a, double* c, double* g, cudaStream_t st);
+namespace {
+
+constexpr int kNoallocMaxN = 32768;  // largest N accepted
+constexpr int kNoallocMaxW = 255;    // largest number of far CTAs (grid - 1)
+constexpr size_t kAlignD = 32;       // 256-byte alignment, in doubles
+
+constexpr size_t align_d(size_t n) { return (n + kAlignD - 1) / kAlignD * kAlignD; }
+constexpr size_t kOffF = 0;
+constexpr size_t kOffB = kOffF + align_d((size_t)(kNoallocMaxN + 1) * kMaxD);
+constexpr size_t kWeightLen = (size_t)kNoallocMaxN + 2 * kPersistB + 2;  // lags 0..N+2B+1
+constexpr size_t kOffA = kOffB + align_d(kWeightLen);
+constexpr size_t kOffC = kOffA + align_d(kWeightLen);
+constexpr size_t kOffG = kOffC + align_d(kWeightLen);
+constexpr size_t kOffPart = kOffG + kAlignD;
+constexpr size_t kOffFlags = kOffPart + align_d((size_t)kPersistRing * kNoallocMaxW * kPersistB * 2 * kMaxD);
+constexpr size_t kScratchDoubles = kOffFlags + kAlignD;  // flags [0..4], status [8]
+
+static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal
+
+void set_msg(char* buf, size_t len, const char* msg) {
+  if (buf && len) std::snprintf(buf, len, "%s", msg);
+}
+
+}  // namespace
+}  // namespace abm
+
+extern "C" abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, int N, const double* params,
+                                        const double* y0, double* Y, double* YP, void* stream, char* errbuf,
+                                        size_t errbuf_len) {
+  using namespace abm;
+  int d = -1, np = -1;
+  switch (sys) {
+    case ABM_SYS_LINEAR: d = 1; np = 3; break;
+    case ABM_SYS_MANUFACTURED: d = 1; np = 9; break;
+    case ABM_SYS_LORENZ: case ABM_SYS_CHEN: case ABM_SYS_ROSSLER: case ABM_SYS_FINANCIAL: d = 3; np = 3; break;
+  }
+  if (d < 0) { set_msg(errbuf, errbuf_len, "abm_solve_noalloc: unknown system"); return ABM_ERR_INVALID_ARG; }
+  if (N < 1 || N > kNoallocMaxN) {
+    char m[160];
+    std::snprintf(m, sizeof m, "abm_solve_noalloc: N = %d outside [1, %d], the size of its static scratch", N,
+                  kNoallocMaxN);
+    set_msg(errbuf, errbuf_len, m);
+    return ABM_ERR_INVALID_ARG;
+  }
+  if (!(std::isfinite(alpha) && alpha > 0.0 && alpha <= 1.0) || !(std::isfinite(h) && h > 0.0) || !params ||
+      !y0 || !Y) {
+    set_msg(errbuf, errbuf_len, "abm_solve_noalloc: need alpha in (0,1], finite h > 0, non-null params/y0/Y");
+    return ABM_ERR_INVALID_ARG;
+  }
+  TrajParams tp{};
+  for (int i = 0; i < np; ++i) {
+    if (!std::isfinite(params[i])) { set_msg(errbuf, errbuf_len, "abm_solve_noalloc: non-finite parameter"); return ABM_ERR_INVALID_ARG; }
+    tp.p[i] = params[i];
+  }
+  for (int i = 0; i < d; ++i) {
+    if (!std::isfinite(y0[i])) { set_msg(errbuf, errbuf_len, "abm_solve_noalloc: non-finite y0"); return ABM_ERR_INVALID_ARG; }
+    tp.y0[i] = y0[i];
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    set_msg(errbuf, errbuf_len, "abm_solve_noalloc: no usable current device");
+    return ABM_ERR_CUDA;
+  }
+  double* base = nullptr;
+  {
+    // once per device, with that device current: the array's device address
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        char m[160];
+        std::snprintf(m, sizeof m, "abm_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        set_msg(errbuf, errbuf_len, m);
+        return ABM_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = (double*)ptr;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  int grid = persistent_max_grid(sys);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  grid = std::min(std::min(grid, sms), kNoallocMaxW + 1);
+  if (grid < 2) { set_msg(errbuf, errbuf_len, "abm_solve_noalloc: fewer than 2 co-resident CTAs"); return ABM_ERR_UNSUPPORTED; }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto cuda_err = [&](cudaError_t e, const char* what) {
+    char m[200];
+    std::snprintf(m, sizeof m, "abm_solve_noalloc: %s: %s", what, cudaGetErrorString(e));
+    set_msg(errbuf, errbuf_len, m);
+    return ABM_ERR_CUDA;
+  };
+  cudaError_t e;
+  double* flags_d = base + kOffFlags;  // [0..4] wait flags, [8] status word
+  // flags and status must start at zero: the array keeps the last call's contents
+  if ((e = cudaMemsetAsync(flags_d, 0, kAlignD * sizeof(double), st)) != cudaSuccess) return cuda_err(e, "memset");
+  if ((e = launch_weights(alpha, (int)kWeightLen - 1, base + kOffB, base + kOffA, base + kOffC, base + kOffG, st)) !=
+      cudaSuccess)
+    return cuda_err(e, "weights kernel");
+  PersistArgs A{};
+  A.F = base + kOffF;
+  A.Y = Y;
+  A.YP = YP;
+  A.b = base + kOffB;
+  A.a = base + kOffA;
+  A.c = base + kOffC;
+  A.g = base + kOffG;
+  A.partial = base + kOffPart;
+  A.flags = reinterpret_cast<unsigned long long*>(flags_d);
+  A.status = reinterpret_cast<unsigned long long*>(flags_d + 8);
+  A.tp = tp;
+  A.alpha = alpha;
+  A.h = h;
+  A.N = N;
+  A.spin_budget = 4000000000LL;
+  A.withhold_tile = -1;
+  if ((e = launch_persistent(sys, A, grid, st)) != cudaSuccess) return cuda_err(e, "persistent kernel");
+  unsigned long long w = 0;
+  if ((e = cudaMemcpyAsync(&w, A.status, sizeof(w), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_err(e, "status read");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_err(e, "stream synchronize");
+  const int code = (int)(w >> 60);
+  if (code) {
+    char m[160];
+    std::snprintf(m, sizeof m, "abm_solve_noalloc: device reported %s at step %llu",
+                  code == ABM_ERR_NONFINITE ? "a non-finite value" : "a wait that ran out", w & 0xFFFFFFFFull);
+    set_msg(errbuf, errbuf_len, m);
+    return (abm_status)code;
+  }
+  set_msg(errbuf, errbuf_len, "");
+  return ABM_OK;
+}
