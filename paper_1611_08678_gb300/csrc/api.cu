@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "batched.cuh"
 #include "common.cuh"
 #include "single.cuh"
@@ -24,6 +26,14 @@ cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long 
                                 cudaStream_t st);
 cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, int n_active, long long s,
                                cudaStream_t st);
+cudaError_t launch_far_tc(int nprod, const FarTcArgs& A, int n_active, cudaStream_t st);
+cudaError_t launch_build_wx(const double* b, const double* a, long long Mw, long long Lbase, long long Lx,
+                            __nv_bfloat16* Wx, cudaStream_t st);
+bool make_tmap_bf16(CUtensorMap* out, void* base, unsigned long long inner, unsigned long long rows,
+                    unsigned box_rows);
+cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long ld, long long plane,
+                            cudaStream_t st);
+cudaError_t launch_sum_partials(const double* far, int ksplit, int n_tiles, double* P, double* C, cudaStream_t st);
 }  // namespace abm
 
 using namespace abm;
@@ -38,6 +48,7 @@ struct WeightSet {
   double alpha = 0.0;
   double *b = nullptr, *a = nullptr, *c = nullptr, *g = nullptr;
   float *b32 = nullptr, *a32 = nullptr;
+  __nv_bfloat16* Wx = nullptr;  // pre-expanded Toeplitz pieces (tensor-core paths)
   unsigned long long last_use = 0;
 };
 
@@ -79,6 +90,12 @@ struct abm_plan_s {
   double* d_bg = nullptr;           // gathered g per bucket
   const double** d_bptr = nullptr;  // [4][kMaxWeightSets] b,a,c pointers
   const float** d_b32ptr = nullptr; // [2][kMaxWeightSets]
+  // tensor-core far history (BF16 split precisions)
+  __nv_bfloat16* Fsh = nullptr;     // [3][max_tiles*96][fsh_ld]
+  long long fsh_ld = 0;
+  long long Lbase = 0, Lx = 0;      // pre-expanded Toeplitz geometry
+  CUtensorMap* d_tmapW = nullptr;   // [kMaxWeightSets][3]
+  CUtensorMap* d_tmapF = nullptr;   // [3]
   unsigned long long* status = nullptr;
   std::string err;
 };
@@ -145,7 +162,47 @@ abm_status get_weights(abm_plan p, double alpha, cudaStream_t st, WeightSet** ou
   slot->last_use = ++p->use_clock;
   CK(launch_weights(alpha, p->Mw, slot->b, slot->a, slot->c, slot->g, st), "weights kernel");
   CK(launch_weights_f32(p->Mw, slot->b, slot->a, slot->b32, slot->a32, st), "weights f32");
+  if (p->Fsh) {
+    if (!slot->Wx) CK(cudaMalloc(&slot->Wx, (size_t)3 * 128 * p->Lx * sizeof(__nv_bfloat16)), "toeplitz pieces");
+    CK(launch_build_wx(slot->b, slot->a, p->Mw, p->Lbase, p->Lx, slot->Wx, st), "toeplitz pieces kernel");
+  }
   *out = slot;
+  return ABM_OK;
+}
+
+
+// abm_far_history on a tensor-core plan: one column tile of 96 columns, history
+// rows [1, s) with s a multiple of 64 (the tensor path always covers whole
+// 64-row blocks from row 0, whose BF16 copy is zero).
+abm_status far_history_tc(abm_plan p, double alpha, const double* F, long long rows, long long cols, long long s,
+                          int B, long long k_lo, long long k_hi, double* P, double* C, cudaStream_t st) {
+  if (cols != 96 || B != 64 || k_lo != 1 || k_hi != s || s % 64 != 0 || s < 64 || s > p->Lbase || rows < s ||
+      p->max_tiles < 1)
+    return fail(p, ABM_ERR_INVALID_ARG,
+                "abm_far_history (tensor-core plan): needs cols = 96, B = 64, k_lo = 1, k_hi = s, s a multiple of 64");
+  WeightSet* w;
+  abm_status rs = get_weights(p, alpha, st, &w);
+  if (rs) return rs;
+  const long long gcols = (long long)p->max_tiles * kTrajPerTile * p->d;
+  CK(launch_fill_fsh(F, s, p->Fsh, p->fsh_ld, gcols * p->fsh_ld, st), "fill history pieces");
+  CUtensorMap mw[3];
+  for (int q = 0; q < 3; ++q)
+    if (!make_tmap_bf16(&mw[q], w->Wx + (size_t)q * 128 * p->Lx, (unsigned long long)p->Lx, 128, 128))
+      return fail(p, ABM_ERR_CUDA, "abm_far_history: tensor map");
+  CK(cudaMemcpyAsync(p->d_tmapW, mw, sizeof(mw), cudaMemcpyHostToDevice, st), "tmaps");
+  TileDesc td{};
+  for (int l = 0; l < kTrajPerTile; ++l) td.traj[l] = l;
+  td.bucket = 0;
+  td.n_tile = (int)s + 64;
+  CK(cudaMemcpyAsync(p->d_tiles, &td, sizeof(td), cudaMemcpyHostToDevice, st), "tile");
+  const int nkb_total = (int)(s / 64);
+  int ks = std::max(1, std::min(nkb_total, 2 * p->sms));
+  while ((size_t)ks * 2 * 64 * 96 > p->farb_cap && ks > 1) --ks;
+  FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
+              p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, 1, ks};
+  CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, 1, st), "tensor-core far kernel");
+  CK(launch_sum_partials(p->farb, ks, 1, P, C, st), "partial sums");
+  CK(cudaStreamSynchronize(st), "synchronize");  // the host-staged tile descriptor must outlive the copy
   return ABM_OK;
 }
 
@@ -169,12 +226,13 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
   *out = nullptr;
   if (sys_dim(sys) < 0 || o->n_max < 1 || o->max_batch < 0 || o->tile_B < 0 || o->far_ctas < 0 ||
       o->spin_timeout_cycles < 0 || (o->prec != ABM_PREC_FP64 && o->prec != ABM_PREC_FP32_FAR &&
-                                     o->prec != ABM_PREC_BF16X3_FAR))
+                                     o->prec != ABM_PREC_BF16X3_FAR && o->prec != ABM_PREC_BF16X6_FAR))
     return ABM_ERR_INVALID_ARG;
   for (int r : o->reserved)
     if (r) return ABM_ERR_INVALID_ARG;
   if (o->tile_B && o->tile_B != 64 && o->tile_B != 32) return ABM_ERR_UNSUPPORTED;
-  if (o->prec == ABM_PREC_BF16X3_FAR) return ABM_ERR_UNSUPPORTED;
+  const bool tc_prec = o->prec == ABM_PREC_BF16X3_FAR || o->prec == ABM_PREC_BF16X6_FAR;
+  if (tc_prec && (sys_dim(sys) != 3 || (o->tile_B && o->tile_B != 64))) return ABM_ERR_UNSUPPORTED;
   abm_plan p = new abm_plan_s();
   p->sys = sys;
   p->d = sys_dim(sys);
@@ -221,7 +279,7 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
     size_t far_units = (size_t)p->max_tiles + 2 * (size_t)p->sms + 16;
     p->farb_cap = far_units * 2 * B * kTrajPerTile * d;
     if (!alloc((void**)&p->Fb, p->fb_cap * sizeof(double)) ||
-        (o->prec != ABM_PREC_FP64 && !alloc((void**)&p->Fb32, p->fb_cap * sizeof(float))) ||
+        (o->prec == ABM_PREC_FP32_FAR && !alloc((void**)&p->Fb32, p->fb_cap * sizeof(float))) ||
         !alloc((void**)&p->farb, p->farb_cap * sizeof(double)) ||
         !alloc((void**)&p->d_tiles, (size_t)p->max_tiles * sizeof(TileDesc)) ||
         !alloc((void**)&p->d_h, (size_t)o->max_batch * sizeof(double)) ||
@@ -232,6 +290,23 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
         !alloc((void**)&p->d_bptr, 3 * kMaxWeightSets * sizeof(double*)) ||
         !alloc((void**)&p->d_b32ptr, 2 * kMaxWeightSets * sizeof(float*)))
       return cleanup_fail(ABM_ERR_OOM);
+    if (tc_prec) {
+      p->Lbase = (long long)((o->n_max + 63) / 64) * 64;
+      p->Lx = p->Lbase + 64;
+      p->fsh_ld = p->Lbase + 64;
+      const size_t gcols = (size_t)p->max_tiles * kTrajPerTile * d;
+      if (!alloc((void**)&p->Fsh, 3 * gcols * p->fsh_ld * sizeof(__nv_bfloat16)) ||
+          !alloc((void**)&p->d_tmapW, (size_t)kMaxWeightSets * 3 * sizeof(CUtensorMap)) ||
+          !alloc((void**)&p->d_tmapF, 3 * sizeof(CUtensorMap)))
+        return cleanup_fail(ABM_ERR_OOM);
+      CUtensorMap mf[3];
+      for (int q = 0; q < 3; ++q)
+        if (!make_tmap_bf16(&mf[q], p->Fsh + (size_t)q * gcols * p->fsh_ld, (unsigned long long)p->fsh_ld, gcols,
+                            (unsigned)(kTrajPerTile * d)))
+          return cleanup_fail(ABM_ERR_CUDA);
+      if (cudaMemcpy(p->d_tmapF, mf, sizeof(mf), cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup_fail(ABM_ERR_CUDA);
+    }
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return cleanup_fail(ABM_ERR_CUDA);
   *out = p;
@@ -242,8 +317,9 @@ abm_status abm_plan_destroy(abm_plan p) {
   if (!p) return ABM_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
   for (auto& w : p->wsets) {
-    cudaFree(w.b); cudaFree(w.a); cudaFree(w.c); cudaFree(w.g); cudaFree(w.b32); cudaFree(w.a32);
+    cudaFree(w.b); cudaFree(w.a); cudaFree(w.c); cudaFree(w.g); cudaFree(w.b32); cudaFree(w.a32); cudaFree(w.Wx);
   }
+  cudaFree(p->Fsh); cudaFree(p->d_tmapW); cudaFree(p->d_tmapF);
   cudaFree(p->ppartial); cudaFree(p->pflags);
   cudaFree(p->F1); cudaFree(p->far1); cudaFree(p->part1); cudaFree(p->tickets); cudaFree(p->hhat1);
   cudaFree(p->Fb); cudaFree(p->Fb32); cudaFree(p->farb); cudaFree(p->d_tiles); cudaFree(p->d_h);
@@ -288,11 +364,12 @@ abm_status abm_far_history(abm_plan p, double alpha, const double* F, long long 
                            long long s, int B, long long k_lo, long long k_hi, double* P, double* C,
                            void* stream) {
   if (!p) return ABM_ERR_INVALID_ARG;
-  if (!alpha_ok(alpha) || !F || !P || !C || rows < 1 || (cols != 1 && cols != 3) || B != p->B ||
+  if (!alpha_ok(alpha) || !F || !P || !C || rows < 1 || (cols != 1 && cols != 3 && !p->Fsh) || B != p->B ||
       k_lo < 1 || k_hi < k_lo || k_hi > s || s >= rows || s + B > p->Mw - 2 * p->B)
     return fail(p, ABM_ERR_INVALID_ARG, "abm_far_history: bad arguments");
-  if (p->o.prec != ABM_PREC_FP64) return fail(p, ABM_ERR_UNSUPPORTED, "abm_far_history: FP64 plans only");
   cudaStream_t st = (cudaStream_t)stream;
+  if (p->Fsh) return far_history_tc(p, alpha, F, rows, cols, s, B, k_lo, k_hi, P, C, st);
+  if (p->o.prec != ABM_PREC_FP64) return fail(p, ABM_ERR_UNSUPPORTED, "abm_far_history: FP64 or tensor-core plans only");
   WeightSet* w;
   abm_status rs = get_weights(p, alpha, st, &w);
   if (rs) return rs;
@@ -410,6 +487,7 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
   }
   if (off > p->fb_cap) return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: history exceeds workspace");
   const int n_tiles = (int)tiles.size();
+  if (p->Fsh && n_tiles > p->max_tiles) return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: too many tiles");
   int ksplit = std::max(1, std::min(16, (2 * p->sms + n_tiles - 1) / n_tiles));
   while ((size_t)ksplit * n_tiles * 2 * B * kTrajPerTile * d > p->farb_cap && ksplit > 1) --ksplit;
   // ---- device tables ----
@@ -430,6 +508,16 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
   CK(cudaMemcpyAsync(p->d_balpha, balpha.data(), balpha.size() * sizeof(double), cudaMemcpyHostToDevice, st), "alpha");
   CK(cudaMemcpyAsync(p->d_bptr, bptr.data(), bptr.size() * sizeof(double*), cudaMemcpyHostToDevice, st), "ptrs");
   CK(cudaMemcpyAsync(p->d_b32ptr, b32ptr.data(), b32ptr.size() * sizeof(float*), cudaMemcpyHostToDevice, st), "ptrs");
+  const bool tc_prec = p->Fsh != nullptr;
+  if (tc_prec) {
+    std::vector<CUtensorMap> mw(ualpha.size() * 3);
+    for (size_t g = 0; g < ualpha.size(); ++g)
+      for (int q = 0; q < 3; ++q)
+        if (!make_tmap_bf16(&mw[g * 3 + q], ws[g]->Wx + (size_t)q * 128 * p->Lx, (unsigned long long)p->Lx, 128,
+                            128))
+          return fail(p, ABM_ERR_CUDA, "abm_solve_batched: tensor map of the Toeplitz pieces");
+    CK(cudaMemcpyAsync(p->d_tmapW, mw.data(), mw.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st), "tmaps");
+  }
   BatchArgs A{};
   A.tiles = p->d_tiles;
   A.n_tiles = n_tiles;
@@ -448,7 +536,10 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
   A.y0 = y0;
   A.hhat = p->d_hhat;
   A.F = p->Fb;
-  A.F32 = (p->o.prec == ABM_PREC_FP64) ? nullptr : p->Fb32;
+  A.F32 = (p->o.prec == ABM_PREC_FP32_FAR) ? p->Fb32 : nullptr;
+  A.Fsh = p->Fsh;
+  A.fsh_ld = p->fsh_ld;
+  A.fsh_plane = (long long)p->max_tiles * kTrajPerTile * d * p->fsh_ld;
   A.far = p->farb;
   A.Y = Y;
   A.YP = YP;
@@ -461,7 +552,19 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
     const long long s = (long long)j * B;
     while (n_active > 0 && tiles[n_active - 1].n_tile <= s) --n_active;
     if (n_active == 0) break;
-    if (s > 1) CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
+    if (s > 1) {
+      if (tc_prec) {
+        const int nkb_total = (int)(s / 64);
+        int ks = std::max(1, std::min(nkb_total, (2 * p->sms + n_active - 1) / n_active));
+        while ((size_t)ks * n_tiles * 2 * B * kTrajPerTile * d > p->farb_cap && ks > 1) --ks;
+        A.ksplit = ks;
+        FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
+                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, n_tiles, ks};
+        CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, n_active, st), "tensor-core far kernel");
+      } else {
+        CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
+      }
+    }
     CK(launch_batched_near(p->sys, A, n_active, s, B, st), "near kernel");
   }
   return ABM_OK;

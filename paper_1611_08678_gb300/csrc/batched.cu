@@ -55,13 +55,30 @@ __global__ void batched_setup_kernel(BatchArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Near kernel: one warp per column tile, one lane per trajectory, nb steps.
+// Near kernel: one CTA per column tile, one warp per state component, one
+// lane per trajectory, nb sequential PECE steps.  Warp c forms the predictor
+// and corrector sums of component c; the components meet through shared
+// memory before each evaluation of f, so the FP64 work of a step is spread
+// over D sub-partitions of the SM.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void split3_bf16(double x, __nv_bfloat16* out) {
+  out[0] = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(out[0]);
+  out[1] = __double2bfloat16(r);
+  r -= (double)__bfloat162float(out[1]);
+  out[2] = __double2bfloat16(r);
+}
+
 template <int SYS>
-__global__ void __launch_bounds__(32) batched_near_kernel(BatchArgs A, long long s, int nb) {
+__global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_kernel(BatchArgs A, long long s, int nb) {
   using S = Sys<SYS>;
-  constexpr int D = S::D, V = 2 * D;
-  const int tile = blockIdx.x, lane = threadIdx.x;
+  constexpr int D = S::D;
+  constexpr int NT = 32 * D;
+  // BF16 split rows s..s+63 of this tile's history, [piece][column][row - s],
+  // written out K-major (128 contiguous bytes per column) at the end
+  __shared__ __align__(16) __nv_bfloat16 stg[3][kTrajPerTile * D][64];
+  __shared__ double ysh[2][D][32], ysh2[2][D][32];  // predictor / corrector exchange
+  const int tile = blockIdx.x, c = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp c = component c
   const TileDesc& T = A.tiles[tile];
   const int traj = T.traj[lane];
   const int src = traj >= 0 ? traj : T.traj[0];
@@ -73,73 +90,86 @@ __global__ void __launch_bounds__(32) batched_near_kernel(BatchArgs A, long long
   const long long Ntraj = traj >= 0 ? (long long)A.N[traj] : 0;
   const double h = A.h[src];
   const double hh = traj >= 0 ? A.hhat[traj] : pow(h, alpha);
-  double p[kMaxParams], y0[D], F0[D];
+  double p[kMaxParams];
 #pragma unroll
   for (int q = 0; q < S::NP; ++q) p[q] = A.params[(size_t)src * S::NP + q];
-#pragma unroll
-  for (int c = 0; c < D; ++c) y0[c] = A.y0[(size_t)src * D + c];
+  const double y0c = A.y0[(size_t)src * D + c];
   double* __restrict__ F = A.F + T.f_off;
   float* __restrict__ F32 = A.F32 ? A.F32 + T.f_off : nullptr;
   constexpr int ld = kTrajPerTile * D;  // row stride of the tile history
-#pragma unroll
-  for (int c = 0; c < D; ++c) F0[c] = F[lane * D + c];
+  const int col = lane * D + c;         // this thread's history column
+  const double F0c = F[col];
   const long long e = s > 1 ? s : 1;  // first near row
-
+  if (A.Fsh) {  // row s: zero for s = 0 (the j = 0 term stays in FP64), else f_s
+    __nv_bfloat16 pc[3];
+    split3_bf16(s == 0 ? 0.0 : F[s * ld + col], pc);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) stg[q][col][0] = pc[q];
+  }
+  bool reported = false;
   for (int i = 0; i < nb; ++i) {
     const long long n = s + i;
-    double sp[D], sc[D];
-    // far part: sum of the K-split partials
-#pragma unroll
-    for (int c = 0; c < D; ++c) { sp[c] = 0.0; sc[c] = 0.0; }
+    const int par = i & 1;
+    // far part: sum of the K-split partials, then the k = 0 terms
+    double sp = 0.0, sc = 0.0;
     if (s > 1) {
       for (int q = 0; q < A.ksplit; ++q) {
-        const double* P = A.far + ((((size_t)q * A.n_tiles + tile) * 2 + 0) * A.B + i) * ld + lane * D;
-        const double* C = A.far + ((((size_t)q * A.n_tiles + tile) * 2 + 1) * A.B + i) * ld + lane * D;
-#pragma unroll
-        for (int c = 0; c < D; ++c) { sp[c] += P[c]; sc[c] += C[c]; }
+        const size_t base = (((size_t)q * A.n_tiles + tile) * 2) * A.B;
+        sp += A.far[(base + i) * ld + col];
+        sc += A.far[(base + A.B + i) * ld + col];
       }
     }
-    // k = 0 terms
-    const double bn = wb[n], cn = wc[n];
-#pragma unroll
-    for (int c = 0; c < D; ++c) { sp[c] = fma(bn, F0[c], sp[c]); sc[c] = fma(cn, F0[c], sc[c]); }
-    // near rows k in [e, n]
+    sp = fma(wb[n], F0c, sp);
+    sc = fma(wc[n], F0c, sc);
+    // near rows k in [e, n], FP64
     for (long long k = e; k <= n; ++k) {
-      const double bw = wb[n - k], aw = wa[n - k];
-      const double* fk = F + k * ld + lane * D;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        double fv = fk[c];
-        sp[c] = fma(bw, fv, sp[c]);
-        sc[c] = fma(aw, fv, sc[c]);
-      }
+      const double fv = F[k * ld + col];
+      sp = fma(wb[n - k], fv, sp);
+      sc = fma(wa[n - k], fv, sc);
     }
     const double t1 = (double)(n + 1) * h;
-    double yp[D], fp[D], y[D], fy[D];
+    const double yp = fma(hh, sp, y0c);
+    ysh[par][c][lane] = yp;
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    double ypv[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) yp[c] = fma(hh, sp[c], y0[c]);
-    S::f(p, alpha, t1, yp, fp);
+    for (int q = 0; q < D; ++q) ypv[q] = ysh[par][q][lane];
+    const double fp = S::fc(c, p, alpha, t1, ypv);
+    const double y = fma(hh, fma(g, fp, sc), y0c);
+    ysh2[par][c][lane] = y;
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    double yv[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) y[c] = fma(hh, fma(g, fp[c], sc[c]), y0[c]);
-    S::f(p, alpha, t1, y, fy);
-    double* Fn = F + (n + 1) * ld + lane * D;
+    for (int q = 0; q < D; ++q) yv[q] = ysh2[par][q][lane];
+    const double fy = S::fc(c, p, alpha, t1, yv);
+    F[(n + 1) * ld + col] = fy;
+    if (F32) F32[(n + 1) * ld + col] = (float)fy;
+    if (A.Fsh && i + 1 < 64) {
+      __nv_bfloat16 pc[3];
+      split3_bf16(fy, pc);
 #pragma unroll
-    for (int c = 0; c < D; ++c) Fn[c] = fy[c];
-    if (F32) {
-#pragma unroll
-      for (int c = 0; c < D; ++c) F32[(n + 1) * ld + lane * D + c] = (float)fy[c];
+      for (int q = 0; q < 3; ++q) stg[q][col][i + 1] = pc[q];
     }
     if (n + 1 <= Ntraj) {
-      double* Yr = A.Y + ((size_t)traj * A.ldY + (n + 1)) * D;
-      bool fin = true;
-#pragma unroll
-      for (int c = 0; c < D; ++c) { Yr[c] = y[c]; fin = fin && isfinite(y[c]) && isfinite(fy[c]); }
-      if (A.YP) {
-        double* YPr = A.YP + ((size_t)traj * A.ldY + (n + 1)) * D;
-#pragma unroll
-        for (int c = 0; c < D; ++c) YPr[c] = yp[c];
+      A.Y[((size_t)traj * A.ldY + (n + 1)) * D + c] = y;
+      if (A.YP) A.YP[((size_t)traj * A.ldY + (n + 1)) * D + c] = yp;
+      if (!reported && !(isfinite(y) && isfinite(fy))) {
+        report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
+        reported = true;
       }
-      if (!fin) report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
+    }
+  }
+  if (A.Fsh) {
+    __syncthreads();
+    // 3 pieces x 32*D columns x 8 chunks of 16 bytes
+    constexpr int CHUNKS = 3 * kTrajPerTile * D * 8;
+    for (int q = threadIdx.x; q < CHUNKS; q += NT) {
+      const int pc = q / (kTrajPerTile * D * 8), rem = q % (kTrajPerTile * D * 8);
+      const int cc = rem / 8, part = rem % 8;
+      const uint4 v = *reinterpret_cast<const uint4*>(&stg[pc][cc][part * 8]);
+      __nv_bfloat16* dst = A.Fsh + (size_t)pc * A.fsh_plane +
+                           ((size_t)blockIdx.x * kTrajPerTile * D + cc) * A.fsh_ld + s + part * 8;
+      *reinterpret_cast<uint4*>(dst) = v;
     }
   }
 }
@@ -268,7 +298,7 @@ cudaError_t launch_batched_setup(int sys, const BatchArgs& A, int n_tiles, cudaS
 
 cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb,
                                 cudaStream_t st) {
-  ABM_DISPATCH_SYSTEM(sys, (batched_near_kernel<SYS><<<n_active, kTrajPerTile, 0, st>>>(A, s, nb)));
+  ABM_DISPATCH_SYSTEM(sys, (batched_near_kernel<SYS><<<n_active, kTrajPerTile * Sys<SYS>::D, 0, st>>>(A, s, nb)));
   return cudaGetLastError();
 }
 

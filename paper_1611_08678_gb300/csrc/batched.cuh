@@ -1,6 +1,9 @@
 // Device-side descriptors of the batched path (built on the host by the
 // scheduler in api.cu, read by the kernels in batched.cu / far_tc.cu).
 #pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace abm {
@@ -35,12 +38,29 @@ struct BatchArgs {
   // histories
   double* F;               // FP64, per tile [rows][32*D]
   float* F32;              // FP32 shadow or null
+  __nv_bfloat16* Fsh;      // BF16 split history [3][n_tiles*32*D][fsh_ld] (K-major) or null
+  long long fsh_ld;        // history rows per column of Fsh
+  long long fsh_plane;     // elements per split piece
   double* far;             // [ksplit][n_tiles][2][B][32*D]
   // outputs
   double* Y;
   double* YP;
   long long ldY;
   unsigned long long* status;
+};
+
+// Arguments of the tensor-core far kernel (far_tc.cu).
+struct FarTcArgs {
+  const TileDesc* tiles;
+  const CUtensorMap* tmapW;  // [bucket][3]: pre-expanded Toeplitz pieces hi, mid, lo
+  const CUtensorMap* tmapF;  // [3]: BF16 split history pieces
+  double* far;               // [ksplit][n_tiles][2][64][96] partial sums
+  unsigned long long* status;
+  long long s;               // time tile start (multiple of 64)
+  long long Lbase;           // x offset base of the pre-expanded Toeplitz
+  long long budget;          // clock cycles per bounded wait
+  int n_tiles;
+  int ksplit;
 };
 
 }  // namespace abm

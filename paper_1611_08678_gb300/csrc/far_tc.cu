@@ -1,0 +1,325 @@
+// A2 on the tensor cores: far-history Toeplitz-tile x F-tile contraction for
+// the batched path, tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation
+// in TMEM) fed by TMA, with the split-precision products of A5.
+//
+// For column tile t (32 trajectories x d components = 96 columns) and time
+// tile s (targets n = s..s+63), the far sums of Sec. 2 over history rows
+// k in [0, s) are one GEMM
+//     D[128 x 96] = W[128 x s] * F[s x 96]
+// with W rows 0..63 the predictor weights b_{s+i-k} (eq. (2)) and rows 64..127
+// the corrector weights a_{s+i-k}, stacked so that both share one F tile.
+// Row k = 0 of the BF16 history is kept zero: the j = 0 terms (b_n f_0,
+// c_n f_0) are added in FP64 by the near kernel.
+//
+// Operands in HBM, both K-major so that a TMA box lands in the 128-byte
+// swizzled layout the MMA reads:
+//   W: "pre-expanded" Toeplitz, Wx[p][r][x] = piece p of w_r(Lbase - x + r%64),
+//      so the tile of time tile s and history block k0 is the plain box at
+//      x = Lbase - s + k0 (a Toeplitz tile is a shifted window of one vector;
+//      storing 128 shifted copies turns it into a regular 2D tile).
+//   F: Fsh[p][t*96 + col][k], written by the near kernel.
+// Split precision: x = x_hi + x_mid + x_lo, each BF16 (successive residuals).
+//   NPROD = 3: hi*hi + hi*mid + mid*hi      (BF16x3 mode)
+//   NPROD = 6: + hi*lo + mid*mid + lo*hi     (BF16x6 mode, FP32-level error)
+// The leading product hi*hi and the correction products accumulate in two
+// separate TMEM accumulators (so the small corrections are not added into a
+// large running sum), each over at most CHUNK_BLOCKS*64 history rows; each
+// chunk is then added into a compensated FP32 pair (TwoSum) by the epilogue
+// warps while the MMAs fill the other TMEM buffer pair.
+//
+// Warp roles (320 threads): warp 0 TMA producer, warp 1 TMEM owner + MMA
+// issuer, warps 2..9 epilogue (lane quarter = warp % 4, column half = (warp-2)/4).
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "batched.cuh"
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace abm {
+
+namespace {
+constexpr int KB = 64;          // history rows per K block (128 bytes of BF16)
+constexpr int CHUNK_BLOCKS = 4; // K blocks per FP32 accumulation chunk (256 rows)
+constexpr int NCOL = 96;        // columns per tile (32 trajectories x 3)
+constexpr int A_BYTES = 128 * KB * 2;
+constexpr int B_BYTES = NCOL * KB * 2;
+constexpr int THREADS = 320;
+
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
+  hi = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(hi);
+  mid = __double2bfloat16(r);
+  r -= (double)__bfloat162float(mid);
+  lo = __double2bfloat16(r);
+}
+}  // namespace
+
+// Pre-expanded Toeplitz weights of one alpha: Wx[p][r][x], p = hi/mid/lo.
+__global__ void build_wx_kernel(const double* __restrict__ b, const double* __restrict__ a, long long Mw,
+                                long long Lbase, long long Lx, __nv_bfloat16* __restrict__ Wx) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 128 * Lx) return;
+  const int r = (int)(idx / Lx);
+  const long long x = idx % Lx;
+  const long long lag = Lbase - x + (r & 63);
+  double w = 0.0;
+  if (lag >= 0 && lag <= Mw) w = (r < 64) ? b[lag] : a[lag];
+  __nv_bfloat16 hi, mid, lo;
+  split3(w, hi, mid, lo);
+  const size_t plane = (size_t)128 * Lx;
+  Wx[idx] = hi;
+  Wx[plane + idx] = mid;
+  Wx[2 * plane + idx] = lo;
+}
+
+
+template <int NPROD>
+__global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
+  constexpr int NA = NPROD == 3 ? 2 : 3;  // W pieces used
+  constexpr int NB = NA;                  // F pieces used
+  constexpr int STAGES = NPROD == 3 ? 3 : 2;
+  constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x, q = blockIdx.y;
+  const int bucket = A.tiles[tile].bucket;
+  const int nkb_total = (int)(A.s / KB);
+  const int per_q = (nkb_total + A.ksplit - 1) / A.ksplit;
+  const int kb_begin = q * per_q;
+  const int nkb = max(0, min(nkb_total, kb_begin + per_q) - kb_begin);
+  const int nchunks = (nkb + CHUNK_BLOCKS - 1) / CHUNK_BLOCKS;
+
+  if (tid == 0) abort_flag = 0;
+  if (warp == 1) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    for (int i = 0; i < STAGES; ++i) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
+    for (int i = 0; i < 2; ++i) { tc::mbar_init(&acc_full[i], 1); tc::mbar_init(&acc_empty[i], 8); }
+    tc::mbar_init(&mma_done, 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0 && nkb > 0) {
+      const CUtensorMap* mW = A.tmapW + bucket * 3;
+      for (int p = 0; p < NA; ++p) tc::prefetch_tmap(mW + p);
+      for (int p = 0; p < NB; ++p) tc::prefetch_tmap(A.tmapF + p);
+      const int ycol = tile * NCOL;
+      for (int i = 0; i < nkb; ++i) {
+        const int st = i % STAGES;
+        if (i >= STAGES && !tc::mbar_wait(&empty[st], ((i / STAGES) - 1) & 1, A.budget, &abort_flag)) {
+          abort_flag = 1;
+          report_status(A.status, ABM_ERR_TIMEOUT, tile, 1000 + i);
+          // wait (bounded) for the loads already issued before giving up
+          for (int j = max(0, i - STAGES); j < i; ++j)
+            tc::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, A.budget, nullptr);
+          break;
+        }
+        uint8_t* sb = smem + st * STAGE_BYTES;
+        tc::mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+        const int k0 = (kb_begin + i) * KB;
+        const int xw = (int)(A.Lbase - A.s) + k0;
+        for (int p = 0; p < NA; ++p) tc::tma_load_2d(sb + p * A_BYTES, mW + p, &full[st], xw, 0);
+        for (int p = 0; p < NB; ++p) tc::tma_load_2d(sb + NA * A_BYTES + p * B_BYTES, A.tmapF + p, &full[st], k0, ycol);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NCOL);
+      // (A piece, B piece) of each product: hi=0, mid=1, lo=2
+      constexpr int PA[6] = {0, 0, 1, 0, 1, 2};
+      constexpr int PB[6] = {0, 1, 0, 2, 1, 0};
+      int i = 0;
+      for (int c = 0; c < nchunks && !abort_flag; ++c) {
+        const int buf = c & 1;
+        if (c >= 2 && !tc::mbar_wait(&acc_empty[buf], ((c / 2) - 1) & 1, A.budget, &abort_flag)) {
+          abort_flag = 1;
+          report_status(A.status, ABM_ERR_TIMEOUT, tile, 2000 + c);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t d_main = tmem + buf * 256, d_corr = d_main + 128;
+        const int iend = min(nkb, (c + 1) * CHUNK_BLOCKS);
+        bool first_main = true, first_corr = true;
+        for (; i < iend; ++i) {
+          const int st = i % STAGES;
+          if (!tc::mbar_wait(&full[st], (i / STAGES) & 1, A.budget, &abort_flag)) {
+            abort_flag = 1;
+            report_status(A.status, ABM_ERR_TIMEOUT, tile, 3000 + i);
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(smem + st * STAGE_BYTES);
+          const uint32_t sbb = sa + NA * A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < KB / 16; ++kk) {
+#pragma unroll
+            for (int pr = 0; pr < NPROD; ++pr) {
+              const uint64_t ad = tc::sdesc_kmajor_sw128(sa + PA[pr] * A_BYTES + kk * 32);
+              const uint64_t bd = tc::sdesc_kmajor_sw128(sbb + PB[pr] * B_BYTES + kk * 32);
+              if (pr == 0) {
+                tc::mma_bf16(d_main, ad, bd, idesc, first_main ? 0u : 1u);
+                first_main = false;
+              } else {
+                tc::mma_bf16(d_corr, ad, bd, idesc, first_corr ? 0u : 1u);
+                first_corr = false;
+              }
+            }
+          }
+          tc::mma_commit(&empty[st]);  // stage reusable once these MMAs have read it
+        }
+        tc::mma_commit(&acc_full[buf]);  // chunk accumulator complete
+      }
+      // every MMA this thread issued has completed before TMEM is released
+      tc::mma_commit(&mma_done);
+      tc::mbar_wait(&mma_done, 0, A.budget, nullptr);
+    }
+  } else {
+    // ---------------- epilogue: 8 warps ----------------
+    const int lq = warp & 3;           // TMEM lane quarter this warp may access
+    const int ch = (warp - 2) >> 2;    // column half: 0 -> cols 0..47, 1 -> 48..95
+    float hi[48], lo[48];
+#pragma unroll
+    for (int j = 0; j < 48; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int buf = c & 1;
+      if (!tc::mbar_wait(&acc_full[buf], (c / 2) & 1, A.budget, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + buf * 256 + ch * 48;
+#pragma unroll
+      for (int g16 = 0; g16 < 3; ++g16) {
+        float v[16];
+        tc::tmem_ld_32x16(base + g16 * 16, v);  // leading products
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {  // (hi, lo) += main  (TwoSum)
+          const int jj = g16 * 16 + j;
+          const float s = hi[jj] + v[j];
+          const float bp = s - hi[jj];
+          lo[jj] += (hi[jj] - (s - bp)) + (v[j] - bp);
+          hi[jj] = s;
+        }
+        tc::tmem_ld_32x16(base + 128 + g16 * 16, v);  // correction products, small: into lo
+#pragma unroll
+        for (int j = 0; j < 16; ++j) lo[g16 * 16 + j] += v[j];
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+    }
+    if (ok) {
+      const int r = lq * 32 + lane;    // accumulator row: 0..63 predictor, 64..127 corrector
+      const int half = r >> 6, i = r & 63;
+      double* out = A.far + ((((size_t)q * A.n_tiles + tile) * 2 + half) * 64 + i) * NCOL + ch * 48;
+#pragma unroll
+      for (int j = 0; j < 48; ++j) out[j] = (double)hi[j] + (double)lo[j];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+// Diagnostic path (abm_far_history): split rows [0, s) of a caller's FP64
+// history F (rows x 96) into the BF16 planes of column tile 0 (row 0 zero).
+__global__ void fill_fsh_kernel(const double* __restrict__ F, long long s, __nv_bfloat16* __restrict__ Fsh,
+                                long long ld, long long plane) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= s * NCOL) return;
+  const long long k = idx / NCOL;
+  const int col = (int)(idx % NCOL);
+  __nv_bfloat16 hi, mid, lo;
+  split3(k == 0 ? 0.0 : F[idx], hi, mid, lo);
+  const size_t o = (size_t)col * ld + k;
+  Fsh[o] = hi;
+  Fsh[plane + o] = mid;
+  Fsh[2 * plane + o] = lo;
+}
+
+// P[i][col] / C[i][col] = sum over the K-split partials of column tile 0.
+__global__ void sum_partials_kernel(const double* __restrict__ far, int ksplit, int n_tiles, double* __restrict__ P,
+                                    double* __restrict__ C) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * 64 * NCOL) return;
+  const int half = idx / (64 * NCOL), rem = idx % (64 * NCOL);
+  double acc = 0.0;
+  for (int q = 0; q < ksplit; ++q) acc += far[(((size_t)q * n_tiles) * 2 + half) * 64 * NCOL + rem];
+  (half == 0 ? P : C)[rem] = acc;
+}
+
+cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long ld, long long plane,
+                            cudaStream_t st) {
+  long long n = s * NCOL;
+  fill_fsh_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, s, Fsh, ld, plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double* far, int ksplit, int n_tiles, double* P, double* C, cudaStream_t st) {
+  sum_partials_kernel<<<(2 * 64 * NCOL + 255) / 256, 256, 0, st>>>(far, ksplit, n_tiles, P, C);
+  return cudaGetLastError();
+}
+
+size_t far_tc_smem_bytes(int nprod) {
+  const int na = nprod == 3 ? 2 : 3, stages = nprod == 3 ? 3 : 2;
+  return (size_t)stages * (na * A_BYTES + na * B_BYTES) + 1024;
+}
+
+cudaError_t launch_build_wx(const double* b, const double* a, long long Mw, long long Lbase, long long Lx,
+                            __nv_bfloat16* Wx, cudaStream_t st) {
+  long long n = 128 * Lx;
+  build_wx_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b, a, Mw, Lbase, Lx, Wx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_far_tc(int nprod, const FarTcArgs& A, int n_active, cudaStream_t st) {
+  const size_t smem = far_tc_smem_bytes(nprod);
+  dim3 grid(n_active, A.ksplit);
+  if (nprod == 3) {
+    cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    far_tc_kernel<3><<<grid, THREADS, smem, st>>>(A);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    far_tc_kernel<6><<<grid, THREADS, smem, st>>>(A);
+  }
+  return cudaGetLastError();
+}
+
+// Host: 2D tiled tensor map, BF16, 128-byte swizzle, box {64, box_rows}.
+bool make_tmap_bf16(CUtensorMap* out, void* base, unsigned long long inner, unsigned long long rows,
+                    unsigned box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) !=
+            cudaSuccess ||
+        !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace abm

@@ -64,7 +64,7 @@ def test_batched_fp32_far_error_reported(abm, system, alphas):
     batch = workloads.random_batch(system, 40, 300, 1100, alphas)
     Y = _run(abm, batch, "fp32").cpu().numpy()
     errs = _errors(batch, Y, t_max=5.0)
-    print(f"{system} fp32-far max rel err (t<=5): {errs.max():.3e}")
+    print(f"{system} fp32 max rel err (t<=5): {errs.max():.3e}")
     assert errs.max() <= 1e-6
 
 
@@ -89,3 +89,49 @@ def test_batched_rejects_bad_arguments(abm):
     big = workloads.random_batch("lorenz", 5, 10, 20, [0.9])
     with pytest.raises(abm.AbmError):
         plan.solve_batched(big.alpha, big.h, big.N, big.params, big.y0)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x6", 2e-6), ("bf16x3", 2e-4)])
+@pytest.mark.parametrize("s", [64, 128, 576, 4096, 8192])
+@pytest.mark.parametrize("data", ["normal", "smooth"])
+def test_far_history_tensor_cores(abm, prec, tol, s, data):
+    """tcgen05 far history (one column tile of 96 columns) against the oracle's
+    FP64 history sums over rows [1, s).  Error model of the split: BF16x6 keeps
+    every product down to 2^-24 (FP32 level), BF16x3 drops products of order
+    2^-16; the tolerance is relative to sum_k |w_k f_k| per output."""
+    alpha, B = 0.93, 64
+    plan = abm.Plan("lorenz", n_max=s + 2 * B, max_batch=32, prec=prec)
+    rng = np.random.default_rng(workloads.SEED_INPUTS + s)
+    if data == "normal":
+        F = rng.standard_normal((s + B + 1, 96))
+    else:  # same-sign, slowly varying columns, like an f history on an attractor lobe
+        k = np.arange(s + B + 1)[:, None]
+        F = (1.0 + rng.uniform(0, 30, 96))[None, :] * (1.2 + np.sin(k / rng.uniform(20, 400, 96)[None, :]))
+    P, C = plan.far_history(alpha, torch.as_tensor(F, device="cuda"), s, B, 1, s)
+    plan.sync()
+    P, C = P.cpu().numpy(), C.cpu().numpy()
+    ob, oa, oc, _ = oracle.weights(alpha, s + B)
+    worst = 0.0
+    for i in range(B):
+        rp, rc = oracle.history(ob, oa, oc, F, s + i, 1, s)
+        lags = s + i - np.arange(1, s)
+        sp = np.abs(ob[lags])[:, None] * np.abs(F[1:s])
+        sc = np.abs(oa[lags])[:, None] * np.abs(F[1:s])
+        worst = max(worst, float(np.max(np.abs(P[i] - rp) / sp.sum(axis=0))),
+                    float(np.max(np.abs(C[i] - rc) / sc.sum(axis=0))))
+    print(f"{prec} {data} s={s}: max error / sum|terms| = {worst:.3e}")
+    assert worst <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x6", 1e-6), ("bf16x3", 1e-4)])
+@pytest.mark.parametrize("system,alphas", [("lorenz", [0.98]), ("rossler", [0.85, 0.9, 1.0]),
+                                           ("financial", [0.95])])
+def test_batched_tensor_core_error_reported(abm, prec, tol, system, alphas):
+    """Tensor-core far history end to end: the max relative error against the
+    FP64 oracle up to t = 5 is printed (the stated error of the mode) and
+    bounded: BF16x6 within 1e-6, BF16x3 within 1e-4."""
+    batch = workloads.random_batch(system, 40, 300, 1100, alphas)
+    Y = _run(abm, batch, prec).cpu().numpy()
+    errs = _errors(batch, Y, t_max=5.0)
+    print(f"{system} {prec} max rel err (t<=5): {errs.max():.3e}")
+    assert errs.max() <= tol
