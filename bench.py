@@ -38,6 +38,19 @@ if ROOT not in sys.path:
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop x max clock
 
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0  # profiling recipe fallback
+
+
+HBM_PEAK_GBS, BF16_PEAK_TFLOPS = _measured_peaks()
+
 # DRAM bytes per launch of the dominant kernel from one ncu capture (see
 # profiles/); None when the kernel changed since the counters were taken.
 NCU_TRAFFIC = {
@@ -67,9 +80,9 @@ def workload(name):
     if name == "lorenz_single":
         return wl.lorenz_single(), "fp64"
     if name == "rossler_batched":
-        return wl.rossler_batched(), "fp32"
+        return wl.rossler_batched(), "bf16x6"
     if name == "financial_batched":
-        return wl.financial_batched(), "fp32"
+        return wl.financial_batched(), "bf16x6"
     raise ValueError(name)
 
 
@@ -268,6 +281,192 @@ def bench_single(args, name, w, world, rank, local):
     return out
 
 
+def tile_schedule(w, per_tile=32):
+    """Column tiles the library forms (alpha groups, N descending, 32 per tile):
+    list of (n_tile, bucket, N of its trajectories)."""
+    import numpy as np
+    tiles = []
+    for g, a in enumerate(np.unique(w.alpha)):
+        idx = np.where(w.alpha == a)[0]
+        Ns = np.sort(w.N[idx])[::-1]
+        for q in range(0, len(Ns), per_tile):
+            tiles.append((int(Ns[q]), g, Ns[q:q + per_tile]))
+    return tiles
+
+
+def far_work(w, nprod, B=64):
+    """Per whole solve: algorithmic far flops (each trajectory's own targets
+    n < N_i times its far rows [1, s)), raw tensor flops the MMAs execute
+    (padded 128 x 96 tiles, all split products) and the operand bytes the far
+    kernel streams from HBM (BF16 history pieces per active tile, Toeplitz
+    pieces per active alpha group)."""
+    import numpy as np
+    tiles = tile_schedule(w)
+    nmax = max(t[0] for t in tiles)
+    npieces = 2 if nprod == 3 else 3
+    alg = raw = byts = 0.0
+    for j in range((nmax + B - 1) // B):
+        s = j * B
+        if s <= 1:
+            continue
+        act = [t for t in tiles if t[0] > s]
+        if not act:
+            break
+        for t in act:
+            targets = np.clip(t[2] - s, 0, B)
+            alg += 2.0 * 2 * (s - 1) * w.d * float(targets.sum())
+        raw += len(act) * 2.0 * 128 * 96 * s * nprod
+        byts += len(act) * s * 96 * 2 * npieces + len({t[1] for t in act}) * 128 * s * 2 * npieces
+    return alg, raw, byts
+
+
+def bench_batched(args, name, w, prec, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1611_08678_gb300 import abm
+    shard = w.subset(np.arange(rank, w.M, world)) if world > 1 else w
+    N = shard.N
+    ldY = int(N.max()) + 1
+    plan = abm.Plan(shard.system, n_max=int(N.max()), max_batch=shard.M, prec=prec, profile=True)
+    params = torch.as_tensor(shard.params, device="cuda")
+    y0 = torch.as_tensor(shard.y0, device="cuda")
+    Y = torch.empty(shard.M, ldY, shard.d, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.solve_batched(shard.alpha, shard.h, N, params, y0, Y=Y, ldY=ldY, sync=False, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    plan.sync(stream)
+    for k in abm.KERNEL_KINDS:
+        plan.kernel_times(k, reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    plan.sync(stream)
+    times = {k: plan.kernel_times(k, reset=True) for k in abm.KERNEL_KINDS}
+    total = sum(a.elapsed_time(b) / 1e3 for a, b in ev)
+    t = torch.tensor([total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_max = float(t.item())
+    steps_all = float(w.N.sum()) * args.steps  # all ranks together
+    value = steps_all / total_max
+    macs_all = w.history_macs() * args.steps
+
+    nprod = 3 if prec == "bf16x3" else 6
+    far_n, far_ms = times["far"]
+    near_n, near_ms = times["near"]
+    if prec.startswith("bf16"):
+        alg, raw, byts = far_work(shard, nprod)
+        far_sec = far_ms / 1e3 / args.steps  # per solve
+        roof = {"bound": "hbm", "achieved": byts / far_sec / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                "frac": byts / far_sec / 1e9 / HBM_PEAK_GBS, "traffic": NCU_TRAFFIC.get(f"{name}_{prec}"),
+                "kernel": f"far_tc_kernel<{nprod}>", "launches_per_solve": far_n / args.steps,
+                "bytes_per_launch": byts / max(1, far_n / args.steps),
+                "algorithmic_tflops": alg / far_sec / 1e12,
+                "tensor_tflops_raw": raw / far_sec / 1e12, "tensor_peak_tflops": BF16_PEAK_TFLOPS,
+                "tensor_frac": raw / far_sec / 1e12 / BF16_PEAK_TFLOPS,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs / bf16_tflops (of measured)"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "kernel": "batched far (SIMT)"}
+
+    # e2e: inputs from pinned host memory, the whole solution back to pinned host memory
+    e2e_steps = 2
+    p_host = torch.as_tensor(shard.params).pin_memory()
+    y_host = torch.as_tensor(shard.y0).pin_memory()
+    Yh = torch.empty(Y.shape, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        params.copy_(p_host, non_blocking=True)
+        y0.copy_(y_host, non_blocking=True)
+        step()
+        Yh.copy_(Y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.sync(stream)
+    e2e_sec = e0.elapsed_time(e1) / 1e3
+    e2e = {"value": float(shard.N.sum()) * e2e_steps * world / e2e_sec, "unit": "trajectory-steps/s",
+           "h2d_bytes_per_step": int(p_host.numel() * 8 + y_host.numel() * 8),
+           "d2h_bytes_per_step": int(Yh.numel() * 8)}
+
+    out = {
+        "metric": "trajectory-steps/s (history MAC/s beside; error vs FP64 oracle stated)",
+        "value": value, "unit": "trajectory-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_max / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"f64 state, {prec} far",
+        "data": "synthetic",
+        "config": {"workload": name, "system": w.system, "trajectories": int(w.M), "trajectories_per_gpu": int(shard.M),
+                   "N_range": [int(w.N.min()), int(w.N.max())], "sum_N": int(w.N.sum()),
+                   "alphas": sorted(set(float(a) for a in w.alpha)), "far_precision": prec,
+                   "parallelism": f"trajectory shards x{world}",
+                   "l2": "inputs larger than L2 (f history of all trajectories, several GB)"},
+        "history_mac_per_s": macs_all / total_max,
+        "roofline": roof,
+        "kernel_ms_per_solve": {k: v[1] / args.steps for k, v in times.items() if v[0]},
+        "e2e": e2e,
+        "gpu_launches": int(sum(v[0] for v in times.values())),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out.update(batched_cpu_baseline(w, Y if world == 1 else None))
+    return out
+
+
+def batched_cpu_baseline(w, Y=None, n_sub=16):
+    """Oracle on a seeded subset (stratified by N), threads over the host
+    cores; scaled by history MACs to the whole workload.  With Y (this run's
+    GPU result, single rank) also the stated error over t <= 5."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle
+    order = np.argsort(w.N)
+    pick = order[np.linspace(0, w.M - 1, n_sub).astype(int)]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+    def run(i):
+        return oracle.solve(w.system, float(w.alpha[i]), float(w.h[i]), int(w.N[i]), w.params[i], w.y0[i])[0]
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        res = list(ex.map(run, pick))
+    sec = time.perf_counter() - t0
+    sub = w.subset(pick)
+    mac_rate = sub.history_macs() / sec
+    value = mac_rate * float(w.N.sum()) / w.history_macs()
+    out = {"cpu_baseline": {"value": value, "unit": "trajectory-steps/s", "cores": int(cores), "kind": "oracle",
+                            "sample": f"{n_sub} trajectories stratified by N ({int(sub.N.sum())} steps, "
+                                      f"{sec:.1f} s on {cores} threads), scaled by history MACs to the workload",
+                            "history_mac_per_s": mac_rate}}
+    if Y is not None:
+        errs = []
+        Yc = Y.cpu().numpy()
+        for i, ref in zip(pick, res):
+            n = min(int(w.N[i]), int(round(5.0 / w.h[i])))
+            errs.append(rel_err(Yc[i, : n + 1], ref[: n + 1]))
+        out["max_rel_err_vs_oracle"] = float(max(errs))
+        out["error_window"] = f"t <= 5 on the {n_sub} oracle trajectories"
+    return out
+
+
 def bench_reference(args, name, w, world, rank):
     """The oracle, as it stands, on the host cores: each step a bounded sample."""
     if rank != 0:
@@ -298,7 +497,8 @@ def bench_reference(args, name, w, world, rank):
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
-    w, _ = workload(args.workload)
+    w, default_prec = workload(args.workload)
+    prec = args.prec or default_prec
     if args.impl == "reference":
         out = bench_reference(args, args.workload, w, world, rank)
         if out is not None:
@@ -311,7 +511,7 @@ def main(argv=None):
     if is_single(args.workload):
         out = bench_single(args, args.workload, w, world, rank, local)
     else:
-        raise SystemExit("batched workloads: see bench_batched (not in this revision)")
+        out = bench_batched(args, args.workload, w, prec, world, rank, local)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

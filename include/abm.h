@@ -98,6 +98,10 @@ typedef struct {
   int test_withhold_tile; /* testing only, 0 = off.  k > 0: in abm_solve the far
                           CTAs never publish tile k-1, so the near CTA's wait
                           runs out and the call reports ABM_ERR_TIMEOUT           */
+  int profile;         /* 1: bracket every kernel launch with CUDA events on the
+                          launching stream (see abm_plan_kernel_times)           */
+  int near_warps;      /* batched near kernel: warps per state component (lag
+                          slices): 0 = chosen from the active tiles, or 1, 2, 4  */
   int reserved[8];     /* must be zero                                            */
 } abm_plan_opts;
 
@@ -182,6 +186,24 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
 abm_status abm_far_history(abm_plan p, double alpha, const double* F, long long rows,
                            long long cols, long long s, int B, long long k_lo, long long k_hi,
                            double* P, double* C, void* stream);
+
+/* Kernel kinds reported by abm_plan_kernel_times. */
+typedef enum {
+  ABM_KERNEL_WEIGHTS = 0,    /* A1 weight generation (and its shadows)            */
+  ABM_KERNEL_FAR = 1,        /* A2 far history of the batched path                */
+  ABM_KERNEL_NEAR = 2,       /* A3 near PECE steps of the batched path            */
+  ABM_KERNEL_SINGLE = 3,     /* the persistent single-trajectory kernel           */
+  ABM_KERNEL_ADJOINT = 4,    /* A6 adjoint kernels                                */
+  ABM_KERNEL_KINDS = 5
+} abm_kernel_kind;
+
+/* Tracing.  Every call counts the kernels it launches per kind; with
+ * opts.profile = 1 each launch is also bracketed by CUDA events on its
+ * stream.  Synchronises `stream`, then returns the launches and the summed
+ * device time in milliseconds (0 without profiling) of one kind since the
+ * last reset; resets that kind's counters when reset != 0. */
+abm_status abm_plan_kernel_times(abm_plan p, abm_kernel_kind kind, void* stream, int reset,
+                                 long long* launches, double* total_ms);
 
 /* abm_solve_noalloc - the single-trajectory solve (abm_solve) for callers
  * that must not allocate device memory: code whose device memory is budgeted

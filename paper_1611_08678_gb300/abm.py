@@ -23,7 +23,9 @@ STATUS = {0: "ABM_OK", 1: "ABM_ERR_INVALID_ARG", 2: "ABM_ERR_CUDA", 3: "ABM_ERR_
 # Every symbol include/abm.h declares (checked by the CPU test suite).
 EXPORTS = ["abm_plan_opts_default", "abm_system_dim", "abm_system_nparams", "abm_plan_create",
            "abm_plan_destroy", "abm_plan_sync", "abm_last_error", "abm_weights", "abm_solve",
-           "abm_solve_batched", "abm_adjoint", "abm_far_history", "abm_solve_noalloc"]
+           "abm_solve_batched", "abm_adjoint", "abm_far_history", "abm_solve_noalloc",
+           "abm_plan_kernel_times"]
+KERNEL_KINDS = {"weights": 0, "far": 1, "near": 2, "single": 3, "adjoint": 4}
 
 
 class AbmError(RuntimeError):
@@ -36,7 +38,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("n_max", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("tile_B", ctypes.c_int), ("far_ctas", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("spin_timeout_cycles", ctypes.c_longlong), ("test_withhold_tile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("profile", ctypes.c_int), ("near_warps", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
 
 
 _lib = None
@@ -72,6 +74,7 @@ def load(path: str = LIB_PATH):
         lib.abm_solve_batched.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_adjoint.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp, _vp, _vp]
         lib.abm_far_history.argtypes = [_vp, D, _vp, LL, LL, LL, I, LL, LL, _vp, _vp, _vp]
+        lib.abm_plan_kernel_times.argtypes = [_vp, I, _vp, I, ctypes.POINTER(LL), ctypes.POINTER(D)]
         lib.abm_solve_noalloc.argtypes = [I, D, D, I, _dp, _dp, _vp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
         for name in EXPORTS:
             if name not in ("abm_plan_opts_default", "abm_last_error", "abm_system_dim", "abm_system_nparams"):
@@ -102,7 +105,7 @@ class Plan:
 
     def __init__(self, system: str, n_max: int, max_batch: int = 0, prec: str = "fp64", tile_B: int = 0,
                  far_ctas: int = 0, use_graph: bool = False, spin_timeout_cycles: int = 0,
-                 test_withhold_tile: int = 0):
+                 test_withhold_tile: int = 0, profile: bool = False, near_warps: int = 0):
         self.lib = load()
         self.system = system
         self.d = self.lib.abm_system_dim(SYSTEMS[system])
@@ -118,6 +121,8 @@ class Plan:
         o.use_graph = int(bool(use_graph))
         o.spin_timeout_cycles = int(spin_timeout_cycles)
         o.test_withhold_tile = int(test_withhold_tile)
+        o.profile = int(bool(profile))
+        o.near_warps = int(near_warps)
         h = _vp()
         st = self.lib.abm_plan_create(ctypes.byref(h), SYSTEMS[system], ctypes.byref(o))
         if st != 0:
@@ -144,6 +149,14 @@ class Plan:
         st = self.lib.abm_plan_sync(self.h, _stream_ptr(stream), ctypes.byref(where))
         self._check(st, "device status")
         return where.value
+
+    def kernel_times(self, kind: str, reset: bool = True, stream=None):
+        """(launches, total device ms) of one kernel kind since the last reset."""
+        n = ctypes.c_longlong(0)
+        ms = ctypes.c_double(0.0)
+        self._check(self.lib.abm_plan_kernel_times(self.h, KERNEL_KINDS[kind], _stream_ptr(stream), int(reset),
+                                                   ctypes.byref(n), ctypes.byref(ms)), "abm_plan_kernel_times")
+        return n.value, ms.value
 
     # -- A1 --
     def weights(self, alpha: float, M: int, stream=None):

@@ -22,7 +22,7 @@ cudaError_t launch_weights_f32(int M, const double* b, const double* a, float* b
                                cudaStream_t st);
 
 cudaError_t launch_batched_setup(int sys, const BatchArgs& A, int n_tiles, cudaStream_t st);
-cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb,
+cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb, int qw,
                                 cudaStream_t st);
 cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, int n_active, long long s,
                                cudaStream_t st);
@@ -98,6 +98,10 @@ struct abm_plan_s {
   CUtensorMap* d_tmapF = nullptr;   // [3]
   unsigned long long* status = nullptr;
   std::string err;
+  // tracing: launches per kernel kind, optional event pairs around each launch
+  long long launches[ABM_KERNEL_KINDS] = {};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  std::vector<std::pair<int, size_t>> ev_used;  // (kind, pool index)
 };
 
 namespace {
@@ -137,6 +141,31 @@ int sys_nparams(abm_system s) {
 
 bool alpha_ok(double a) { return std::isfinite(a) && a > 0.0 && a <= 1.0; }
 
+// Tracing: opens an event pair before a launch of `kind` (when profiling) and
+// closes it after; counts the launch.
+struct Trace {
+  abm_plan p;
+  int kind;
+  cudaStream_t st;
+  size_t idx = (size_t)-1;
+  Trace(abm_plan p_, int kind_, cudaStream_t st_) : p(p_), kind(kind_), st(st_) {
+    p->launches[kind] += 1;
+    if (!p->o.profile) return;
+    if (p->ev_used.size() >= p->ev_pool.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+      p->ev_pool.push_back({a, b});
+    }
+    idx = p->ev_used.size();
+    p->ev_used.push_back({kind, idx});
+    cudaEventRecord(p->ev_pool[idx].first, st);
+  }
+  ~Trace() {
+    if (idx != (size_t)-1) cudaEventRecord(p->ev_pool[idx].second, st);
+  }
+};
+
 // Weight vectors for one alpha (cached; least recently used set is reused).
 abm_status get_weights(abm_plan p, double alpha, cudaStream_t st, WeightSet** out) {
   for (auto& w : p->wsets)
@@ -160,11 +189,13 @@ abm_status get_weights(abm_plan p, double alpha, cudaStream_t st, WeightSet** ou
   }
   slot->alpha = alpha;
   slot->last_use = ++p->use_clock;
-  CK(launch_weights(alpha, p->Mw, slot->b, slot->a, slot->c, slot->g, st), "weights kernel");
-  CK(launch_weights_f32(p->Mw, slot->b, slot->a, slot->b32, slot->a32, st), "weights f32");
-  if (p->Fsh) {
-    if (!slot->Wx) CK(cudaMalloc(&slot->Wx, (size_t)3 * 128 * p->Lx * sizeof(__nv_bfloat16)), "toeplitz pieces");
-    CK(launch_build_wx(slot->b, slot->a, p->Mw, p->Lbase, p->Lx, slot->Wx, st), "toeplitz pieces kernel");
+  if (p->Fsh && !slot->Wx)
+    CK(cudaMalloc(&slot->Wx, (size_t)3 * 128 * p->Lx * sizeof(__nv_bfloat16)), "toeplitz pieces");
+  {
+    Trace tr(p, ABM_KERNEL_WEIGHTS, st);
+    CK(launch_weights(alpha, p->Mw, slot->b, slot->a, slot->c, slot->g, st), "weights kernel");
+    CK(launch_weights_f32(p->Mw, slot->b, slot->a, slot->b32, slot->a32, st), "weights f32");
+    if (p->Fsh) CK(launch_build_wx(slot->b, slot->a, p->Mw, p->Lbase, p->Lx, slot->Wx, st), "toeplitz pieces kernel");
   }
   *out = slot;
   return ABM_OK;
@@ -196,8 +227,8 @@ abm_status far_history_tc(abm_plan p, double alpha, const double* F, long long r
   td.n_tile = (int)s + 64;
   CK(cudaMemcpyAsync(p->d_tiles, &td, sizeof(td), cudaMemcpyHostToDevice, st), "tile");
   const int nkb_total = (int)(s / 64);
-  int ks = std::max(1, std::min(nkb_total, 2 * p->sms));
-  while ((size_t)ks * 2 * 64 * 96 > p->farb_cap && ks > 1) --ks;
+  const int ks = std::max(1, std::min(nkb_total, 2 * p->sms));
+  CK(cudaMemsetAsync(p->farb, 0, (size_t)2 * 64 * 96 * sizeof(double), st), "far sums reset");
   FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
               p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, 1, ks};
   CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, 1, st), "tensor-core far kernel");
@@ -231,6 +262,8 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
   for (int r : o->reserved)
     if (r) return ABM_ERR_INVALID_ARG;
   if (o->tile_B && o->tile_B != 64 && o->tile_B != 32) return ABM_ERR_UNSUPPORTED;
+  if (o->near_warps != 0 && o->near_warps != 1 && o->near_warps != 2 && o->near_warps != 4)
+    return ABM_ERR_INVALID_ARG;
   const bool tc_prec = o->prec == ABM_PREC_BF16X3_FAR || o->prec == ABM_PREC_BF16X6_FAR;
   if (tc_prec && (sys_dim(sys) != 3 || (o->tile_B && o->tile_B != 64))) return ABM_ERR_UNSUPPORTED;
   abm_plan p = new abm_plan_s();
@@ -331,6 +364,7 @@ abm_status abm_plan_destroy(abm_plan p) {
     if (p->ev_far[i]) cudaEventDestroy(p->ev_far[i]);
   }
   if (p->ev_start) cudaEventDestroy(p->ev_start);
+  for (auto& e : p->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   delete p;
   return ABM_OK;
 }
@@ -430,7 +464,10 @@ abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* pa
   A.N = N;
   A.spin_budget = p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL;
   A.withhold_tile = p->o.test_withhold_tile > 0 ? p->o.test_withhold_tile - 1 : -1;
-  CK(launch_persistent(p->sys, A, p->Gp, st), "persistent single-trajectory kernel");
+  {
+    Trace tr(p, ABM_KERNEL_SINGLE, st);
+    CK(launch_persistent(p->sys, A, p->Gp, st), "persistent single-trajectory kernel");
+  }
   return ABM_OK;
 }
 
@@ -552,20 +589,65 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
     const long long s = (long long)j * B;
     while (n_active > 0 && tiles[n_active - 1].n_tile <= s) --n_active;
     if (n_active == 0) break;
+    A.n_tiles = n_active;  // far partials of this time tile: [ksplit][n_active][2][B][cols]
     if (s > 1) {
       if (tc_prec) {
         const int nkb_total = (int)(s / 64);
-        int ks = std::max(1, std::min(nkb_total, (2 * p->sms + n_active - 1) / n_active));
-        while ((size_t)ks * n_tiles * 2 * B * kTrajPerTile * d > p->farb_cap && ks > 1) --ks;
-        A.ksplit = ks;
+        const int ks = std::max(1, std::min(nkb_total, (2 * p->sms + n_active - 1) / n_active));
+        A.ksplit = 1;  // the K-split parts are added on the device
+        CK(cudaMemsetAsync(p->farb, 0, (size_t)n_active * 2 * B * kTrajPerTile * d * sizeof(double), st),
+           "far sums reset");
         FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
-                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, n_tiles, ks};
+                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, n_active, ks};
+        Trace tr(p, ABM_KERNEL_FAR, st);
         CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, n_active, st), "tensor-core far kernel");
       } else {
+        Trace tr(p, ABM_KERNEL_FAR, st);
         CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
       }
     }
-    CK(launch_batched_near(p->sys, A, n_active, s, B, st), "near kernel");
+    {
+      Trace tr(p, ABM_KERNEL_NEAR, st);
+      // warps per component: latency when few tiles are active, throughput when many
+      const int qw = p->o.near_warps ? p->o.near_warps
+                                     : (n_active <= p->sms ? 4 : (n_active <= 2 * p->sms ? 2 : 1));
+      CK(launch_batched_near(p->sys, A, n_active, s, B, qw, st), "near kernel");
+    }
+  }
+  return ABM_OK;
+}
+
+abm_status abm_plan_kernel_times(abm_plan p, abm_kernel_kind kind, void* stream, int reset, long long* launches,
+                                 double* total_ms) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if ((int)kind < 0 || (int)kind >= ABM_KERNEL_KINDS) return fail(p, ABM_ERR_INVALID_ARG, "unknown kernel kind");
+  CK(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+  CK(cudaDeviceSynchronize(), "device synchronize");
+  double ms = 0.0;
+  std::vector<std::pair<int, size_t>> keep;
+  for (auto& u : p->ev_used) {
+    if (u.first != (int)kind) { keep.push_back(u); continue; }
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->ev_pool[u.second].first, p->ev_pool[u.second].second) == cudaSuccess) ms += t;
+    if (!reset) keep.push_back(u);
+  }
+  if (launches) *launches = p->launches[kind];
+  if (total_ms) *total_ms = ms;
+  if (reset) {
+    p->launches[kind] = 0;
+    // event pairs of the reset kind become free again: rebuild the used list
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+    std::vector<std::pair<int, size_t>> used;
+    std::vector<bool> taken(p->ev_pool.size(), false);
+    for (auto& u : keep) {
+      used.push_back({u.first, pool.size()});
+      pool.push_back(p->ev_pool[u.second]);
+      taken[u.second] = true;
+    }
+    for (size_t i = 0; i < p->ev_pool.size(); ++i)
+      if (!taken[i]) pool.push_back(p->ev_pool[i]);
+    p->ev_pool.swap(pool);
+    p->ev_used.swap(used);
   }
   return ABM_OK;
 }

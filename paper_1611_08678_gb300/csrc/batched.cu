@@ -55,11 +55,13 @@ __global__ void batched_setup_kernel(BatchArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Near kernel: one CTA per column tile, one warp per state component, one
-// lane per trajectory, nb sequential PECE steps.  Warp c forms the predictor
-// and corrector sums of component c; the components meet through shared
-// memory before each evaluation of f, so the FP64 work of a step is spread
-// over D sub-partitions of the SM.
+// Near kernel: one CTA per column tile, nb sequential PECE steps in FP64, one
+// lane per trajectory.  QW warps per state component each sum one slice of
+// the window lags (rows k with k - e = q mod QW) out of a shared-memory copy
+// of the tile's f rows; warp q = 0 of component c adds the slices and runs the
+// chain for that component (y^P, f(y^P), y, f(y)); the components meet
+// through shared memory before each evaluation of f.  QW trades FP64 latency
+// per step (few tiles) against throughput (many tiles per SM).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void split3_bf16(double x, __nv_bfloat16* out) {
   out[0] = __double2bfloat16(x);
@@ -69,16 +71,24 @@ __device__ __forceinline__ void split3_bf16(double x, __nv_bfloat16* out) {
   out[2] = __double2bfloat16(r);
 }
 
-template <int SYS>
-__global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_kernel(BatchArgs A, long long s, int nb) {
+template <int SYS, int QW>
+__global__ void __launch_bounds__(32 * QW * Sys<SYS>::D) batched_near_kernel(BatchArgs A, long long s, int nb) {
   using S = Sys<SYS>;
   constexpr int D = S::D;
-  constexpr int NT = 32 * D;
-  // BF16 split rows s..s+63 of this tile's history, [piece][column][row - s],
-  // written out K-major (128 contiguous bytes per column) at the end
-  __shared__ __align__(16) __nv_bfloat16 stg[3][kTrajPerTile * D][64];
+  constexpr int NT = 32 * QW * D;
+  constexpr int ld = kTrajPerTile * D;  // columns of the tile history
+  // dynamic shared memory: f rows s..s+64 of this tile (FP64, the window every
+  // sum reads) and the window partial sums of each lag slice
+  extern __shared__ double near_dyn[];
+  double (*Fw)[ld] = reinterpret_cast<double (*)[ld]>(near_dyn);
+  double (*Rp)[ld] = reinterpret_cast<double (*)[ld]>(near_dyn + 65 * ld);
+  double (*Rc)[ld] = reinterpret_cast<double (*)[ld]>(near_dyn + (65 + QW) * ld);
   __shared__ double ysh[2][D][32], ysh2[2][D][32];  // predictor / corrector exchange
-  const int tile = blockIdx.x, c = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp c = component c
+  __shared__ double wsb[65], wsa[65];               // lags 0..64 of this tile's weights
+  __shared__ double bns[64], cns[64];               // b_n, c_n of this tile's targets
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = warp % D, q = warp / D;  // component, lag slice
+  const int tile = blockIdx.x;
   const TileDesc& T = A.tiles[tile];
   const int traj = T.traj[lane];
   const int src = traj >= 0 ? traj : T.traj[0];
@@ -92,84 +102,119 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_kernel(BatchArg
   const double hh = traj >= 0 ? A.hhat[traj] : pow(h, alpha);
   double p[kMaxParams];
 #pragma unroll
-  for (int q = 0; q < S::NP; ++q) p[q] = A.params[(size_t)src * S::NP + q];
+  for (int k = 0; k < S::NP; ++k) p[k] = A.params[(size_t)src * S::NP + k];
   const double y0c = A.y0[(size_t)src * D + c];
   double* __restrict__ F = A.F + T.f_off;
   float* __restrict__ F32 = A.F32 ? A.F32 + T.f_off : nullptr;
-  constexpr int ld = kTrajPerTile * D;  // row stride of the tile history
-  const int col = lane * D + c;         // this thread's history column
+  const int col = lane * D + c;  // this thread's history column
   const double F0c = F[col];
-  const long long e = s > 1 ? s : 1;  // first near row
-  if (A.Fsh) {  // row s: zero for s = 0 (the j = 0 term stays in FP64), else f_s
-    __nv_bfloat16 pc[3];
-    split3_bf16(s == 0 ? 0.0 : F[s * ld + col], pc);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) stg[q][col][0] = pc[q];
+  if (q == 0) Fw[0][col] = F[s * ld + col];
+  for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
+  for (int m = threadIdx.x; m < 64; m += NT) { bns[m] = wb[s + m]; cns[m] = wc[s + m]; }
+  const int kfirst = s > 1 ? 0 : 1;  // window rows relative to s (row 0 is f_0 when s = 0)
+  const double* __restrict__ farP = A.far + (((size_t)tile * 2) * A.B) * ld + col;
+  const size_t far_q_stride = (size_t)A.n_tiles * 2 * A.B * ld;
+  const size_t far_c_off = (size_t)A.B * ld;
+  // far partial sums + k = 0 terms of the next target, loaded a step ahead
+  double nxp = 0.0, nxc = 0.0;
+  if (q == 0 && s > 1) {
+    for (int kq = 0; kq < A.ksplit; ++kq) {
+      nxp += farP[kq * far_q_stride];
+      nxc += farP[kq * far_q_stride + far_c_off];
+    }
   }
   bool reported = false;
+  __syncthreads();
   for (int i = 0; i < nb; ++i) {
     const long long n = s + i;
     const int par = i & 1;
-    // far part: sum of the K-split partials, then the k = 0 terms
-    double sp = 0.0, sc = 0.0;
-    if (s > 1) {
-      for (int q = 0; q < A.ksplit; ++q) {
-        const size_t base = (((size_t)q * A.n_tiles + tile) * 2) * A.B;
-        sp += A.far[(base + i) * ld + col];
-        sc += A.far[(base + A.B + i) * ld + col];
+    // slice q of the window sums over rows r in [kfirst, i] (r = q mod QW);
+    // two accumulator chains per sum
+    double sp0 = 0.0, sc0 = 0.0, sp1 = 0.0, sc1 = 0.0;
+    if (q == 0) {
+      sp0 = fma(bns[i], F0c, nxp);
+      sc0 = fma(cns[i], F0c, nxc);
+      nxp = nxc = 0.0;
+      if (s > 1 && i + 1 < nb) {
+        for (int kq = 0; kq < A.ksplit; ++kq) {
+          nxp += farP[kq * far_q_stride + (size_t)(i + 1) * ld];
+          nxc += farP[kq * far_q_stride + far_c_off + (size_t)(i + 1) * ld];
+        }
       }
     }
-    sp = fma(wb[n], F0c, sp);
-    sc = fma(wc[n], F0c, sc);
-    // near rows k in [e, n], FP64
-    for (long long k = e; k <= n; ++k) {
-      const double fv = F[k * ld + col];
-      sp = fma(wb[n - k], fv, sp);
-      sc = fma(wa[n - k], fv, sc);
+    int r = kfirst + ((q - kfirst) % QW + QW) % QW;
+    for (; r + QW <= i; r += 2 * QW) {
+      const double f0 = Fw[r][col], f1 = Fw[r + QW][col];
+      sp0 = fma(wsb[i - r], f0, sp0);
+      sc0 = fma(wsa[i - r], f0, sc0);
+      sp1 = fma(wsb[i - r - QW], f1, sp1);
+      sc1 = fma(wsa[i - r - QW], f1, sc1);
     }
-    const double t1 = (double)(n + 1) * h;
-    const double yp = fma(hh, sp, y0c);
-    ysh[par][c][lane] = yp;
-    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
-    double ypv[D];
-#pragma unroll
-    for (int q = 0; q < D; ++q) ypv[q] = ysh[par][q][lane];
-    const double fp = S::fc(c, p, alpha, t1, ypv);
-    const double y = fma(hh, fma(g, fp, sc), y0c);
-    ysh2[par][c][lane] = y;
-    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
-    double yv[D];
-#pragma unroll
-    for (int q = 0; q < D; ++q) yv[q] = ysh2[par][q][lane];
-    const double fy = S::fc(c, p, alpha, t1, yv);
-    F[(n + 1) * ld + col] = fy;
-    if (F32) F32[(n + 1) * ld + col] = (float)fy;
-    if (A.Fsh && i + 1 < 64) {
-      __nv_bfloat16 pc[3];
-      split3_bf16(fy, pc);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) stg[q][col][i + 1] = pc[q];
+    if (r <= i) {
+      const double f0 = Fw[r][col];
+      sp0 = fma(wsb[i - r], f0, sp0);
+      sc0 = fma(wsa[i - r], f0, sc0);
     }
-    if (n + 1 <= Ntraj) {
-      A.Y[((size_t)traj * A.ldY + (n + 1)) * D + c] = y;
-      if (A.YP) A.YP[((size_t)traj * A.ldY + (n + 1)) * D + c] = yp;
-      if (!reported && !(isfinite(y) && isfinite(fy))) {
-        report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
-        reported = true;
+    double sp = sp0 + sp1, sc = sc0 + sc1;
+    if (QW > 1) {
+      Rp[q][col] = sp;
+      Rc[q][col] = sc;
+      __syncthreads();
+    }
+    if (q == 0) {  // the chain: component c
+      if (QW > 1) {
+#pragma unroll
+        for (int k = 1; k < QW; ++k) { sp += Rp[k][col]; sc += Rc[k][col]; }
+      }
+      const double t1 = (double)(n + 1) * h;
+      const double yp = fma(hh, sp, y0c);
+      ysh[par][c][lane] = yp;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
+      double ypv[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) ypv[k] = ysh[par][k][lane];
+      const double fp = S::fc(c, p, alpha, t1, ypv);
+      const double y = fma(hh, fma(g, fp, sc), y0c);
+      ysh2[par][c][lane] = y;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
+      double yv[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) yv[k] = ysh2[par][k][lane];
+      const double fy = S::fc(c, p, alpha, t1, yv);
+      Fw[i + 1][col] = fy;
+      F[(n + 1) * ld + col] = fy;
+      if (F32) F32[(n + 1) * ld + col] = (float)fy;
+      if (n + 1 <= Ntraj) {
+        A.Y[((size_t)traj * A.ldY + (n + 1)) * D + c] = y;
+        if (A.YP) A.YP[((size_t)traj * A.ldY + (n + 1)) * D + c] = yp;
+        if (!reported && !(isfinite(y) && isfinite(fy))) {
+          report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
+          reported = true;
+        }
       }
     }
+    if (QW > 1) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
   }
+  __syncthreads();
   if (A.Fsh) {
-    __syncthreads();
-    // 3 pieces x 32*D columns x 8 chunks of 16 bytes
-    constexpr int CHUNKS = 3 * kTrajPerTile * D * 8;
-    for (int q = threadIdx.x; q < CHUNKS; q += NT) {
-      const int pc = q / (kTrajPerTile * D * 8), rem = q % (kTrajPerTile * D * 8);
+    // BF16 split of rows s..s+63, K-major: 8 rows of one column and piece per
+    // 16-byte store (row s of the first tile stays zero: the j = 0 term is FP64)
+    constexpr int UNITS = 3 * ld * 8;
+    for (int u = threadIdx.x; u < UNITS; u += NT) {
+      const int pc = u / (ld * 8), rem = u % (ld * 8);
       const int cc = rem / 8, part = rem % 8;
-      const uint4 v = *reinterpret_cast<const uint4*>(&stg[pc][cc][part * 8]);
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int row = part * 8 + r;
+        __nv_bfloat16 pcs[3];
+        split3_bf16((s == 0 && row == 0) ? 0.0 : Fw[row][cc], pcs);
+        v[r] = pcs[pc];
+      }
       __nv_bfloat16* dst = A.Fsh + (size_t)pc * A.fsh_plane +
-                           ((size_t)blockIdx.x * kTrajPerTile * D + cc) * A.fsh_ld + s + part * 8;
-      *reinterpret_cast<uint4*>(dst) = v;
+                           ((size_t)blockIdx.x * ld + cc) * A.fsh_ld + s + part * 8;
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
     }
   }
 }
@@ -296,10 +341,32 @@ cudaError_t launch_batched_setup(int sys, const BatchArgs& A, int n_tiles, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb,
-                                cudaStream_t st) {
-  ABM_DISPATCH_SYSTEM(sys, (batched_near_kernel<SYS><<<n_active, kTrajPerTile * Sys<SYS>::D, 0, st>>>(A, s, nb)));
+template <int SYS, int QW>
+cudaError_t launch_near_t(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+  constexpr int D = Sys<SYS>::D;
+  const size_t smem = (size_t)(65 + 2 * QW) * kTrajPerTile * D * sizeof(double);
+  static bool attr_set = false;  // per instantiation; a plan is used from one thread
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(batched_near_kernel<SYS, QW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  batched_near_kernel<SYS, QW><<<n_active, 32 * QW * D, smem, st>>>(A, s, nb);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb, int qw,
+                                cudaStream_t st) {
+  cudaError_t err = cudaErrorInvalidValue;
+  if (qw == 4) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 4>(A, n_active, s, nb, st)));
+  } else if (qw == 2) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 2>(A, n_active, s, nb, st)));
+  } else {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 1>(A, n_active, s, nb, st)));
+  }
+  return err;
 }
 
 cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, int n_active, long long s,

@@ -54,7 +54,8 @@ struct FarTcArgs {
   const TileDesc* tiles;
   const CUtensorMap* tmapW;  // [bucket][3]: pre-expanded Toeplitz pieces hi, mid, lo
   const CUtensorMap* tmapF;  // [3]: BF16 split history pieces
-  double* far;               // [ksplit][n_tiles][2][64][96] partial sums
+  double* far;               // [n_tiles][2][64][96] sums, zeroed before the launch; the
+                             // ksplit CTAs of a tile add their parts with FP64 atomics
   unsigned long long* status;
   long long s;               // time tile start (multiple of 64)
   long long Lbase;           // x offset base of the pre-expanded Toeplitz

@@ -221,12 +221,13 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
     }
-    if (ok) {
+    if (ok && nkb > 0) {
+      // the K-split CTAs of a tile add into one FP64 sum (zeroed before the launch)
       const int r = lq * 32 + lane;    // accumulator row: 0..63 predictor, 64..127 corrector
       const int half = r >> 6, i = r & 63;
-      double* out = A.far + ((((size_t)q * A.n_tiles + tile) * 2 + half) * 64 + i) * NCOL + ch * 48;
+      double* out = A.far + (((size_t)tile * 2 + half) * 64 + i) * NCOL + ch * 48;
 #pragma unroll
-      for (int j = 0; j < 48; ++j) out[j] = (double)hi[j] + (double)lo[j];
+      for (int j = 0; j < 48; ++j) atomicAdd(out + j, (double)hi[j] + (double)lo[j]);
     }
   }
   tc::fence_before_sync();
@@ -256,9 +257,7 @@ __global__ void sum_partials_kernel(const double* __restrict__ far, int ksplit, 
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 2 * 64 * NCOL) return;
   const int half = idx / (64 * NCOL), rem = idx % (64 * NCOL);
-  double acc = 0.0;
-  for (int q = 0; q < ksplit; ++q) acc += far[(((size_t)q * n_tiles) * 2 + half) * 64 * NCOL + rem];
-  (half == 0 ? P : C)[rem] = acc;
+  (half == 0 ? P : C)[rem] = far[(size_t)half * 64 * NCOL + rem];
 }
 
 cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long ld, long long plane,
@@ -288,13 +287,20 @@ cudaError_t launch_build_wx(const double* b, const double* a, long long Mw, long
 cudaError_t launch_far_tc(int nprod, const FarTcArgs& A, int n_active, cudaStream_t st) {
   const size_t smem = far_tc_smem_bytes(nprod);
   dim3 grid(n_active, A.ksplit);
+  static bool attr3 = false, attr6 = false;  // set once per instantiation
   if (nprod == 3) {
-    cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (!attr3) {
+      cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr3 = true;
+    }
     far_tc_kernel<3><<<grid, THREADS, smem, st>>>(A);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (!attr6) {
+      cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr6 = true;
+    }
     far_tc_kernel<6><<<grid, THREADS, smem, st>>>(A);
   }
   return cudaGetLastError();
