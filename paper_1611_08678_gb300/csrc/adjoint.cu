@@ -1,0 +1,266 @@
+// A6 - discrete adjoint of the batched ABM solve (the paper has no adjoint;
+// this differentiates exactly the scheme of Sec. 2).
+//
+// Forward (per trajectory): y^P_{n+1} = y0 + h^a sum_{k<=n} b_{n-k} f_k,
+// y_{n+1} = y0 + h^a (c_n f_0 + sum_{1<=k<=n} a_{n-k} f_k + g f(t_{n+1}, y^P_{n+1})),
+// f_k = f(t_k, y_k), loss L(y_0..y_N) with partials G_n = dL/dy_n (given).
+// Reverse sweep over k = N..0 with lambda_k = dL/dy_k, mu_k = dL/dy^P_k,
+// phi_k = dL/df_k (all total derivatives):
+//   phi_k    = h^a sum_{n>k} (b_{n-1-k} mu_n + a_{n-1-k} lambda_n)   (k >= 1; phi_N = 0)
+//   phi_0    = h^a sum_{n>=1} (b_{n-1} mu_n + c_{n-1} lambda_n)
+//   lambda_k = G_k + J(t_k, y_k)^T phi_k
+//   mu_k     = h^a g J(t_k, y^P_k)^T lambda_k                         (k >= 1)
+//   dL/dp    = sum_k Q(t_k, y_k)^T phi_k + h^a g sum_{k>=1} Q(t_k, y^P_k)^T lambda_k
+//   dL/dy0   = G_0 + J(0, y_0)^T phi_0 + sum_{k>=1} (lambda_k + mu_k)
+// (J = df/dy, Q = df/dp, recomputed from the stored y_k and y^P_k; no
+// Jacobian is stored.)  In reversed time r = N - k the phi sum is the same
+// Toeplitz contraction as the forward history sums: for target t = r - 1,
+//   phi = h^a (sum_{r' <= t} b_{t-r'} mu~_{r'} + sum_{r' <= t} a_{t-r'} lambda~_{r'}),
+// so the batched machinery is reused: each forward column tile becomes two
+// adjoint tiles (mu~ and lambda~ histories), the far kernels (tensor-core or
+// FP64) produce the far sums, and the near kernel below runs the reverse
+// steps with the window lags in FP64.
+#include "batched.cuh"
+#include "common.cuh"
+#include "systems.cuh"
+
+namespace abm {
+
+
+namespace {
+__device__ __forceinline__ void split3_bf16_adj(double x, __nv_bfloat16* out) {
+  out[0] = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(out[0]);
+  out[1] = __double2bfloat16(r);
+  r -= (double)__bfloat162float(out[1]);
+  out[2] = __double2bfloat16(r);
+}
+template <int D>
+__device__ __forceinline__ void bar_components() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
+}
+}  // namespace
+
+// k = N_i: lambda_N = G_N, mu_N = h^a g JP^T lambda_N; row 0 of both histories.
+template <int SYS>
+__global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_setup_kernel(AdjArgs A) {
+  using S = Sys<SYS>;
+  constexpr int D = S::D, NP = S::NP, ld = kTrajPerTile * D;
+  __shared__ double lsh[D][32];
+  const int tile = blockIdx.x, c = threadIdx.x >> 5, lane = threadIdx.x & 31, col = lane * D + c;
+  const TileDesc& T = A.tiles[tile];
+  const int traj = T.traj[lane];
+  const int src = traj >= 0 ? traj : T.traj[0];
+  const double alpha = A.bucket_alpha[T.bucket];
+  const double g = A.bucket_g[T.bucket];
+  const double* wc = A.bucket_c[T.bucket];
+  const long long N = A.N[src];
+  const double h = A.h[src];
+  const double hh = pow(h, alpha);
+  double p[kMaxParams];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) p[q] = A.params[(size_t)src * NP + q];
+  const double* yPN = A.YP + ((size_t)src * A.ldY + N) * D;
+  double yp[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) yp[q] = yPN[q];
+  const double lam = A.G[((size_t)src * A.ldY + N) * D + c];
+  lsh[c][lane] = lam;
+  bar_components<D>();
+  double J[D * D], Q[D * NP];
+  S::jac(p, alpha, (double)N * h, yp, J, Q);
+  double jl = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) jl = fma(J[j * D + c], lsh[j][lane], jl);
+  const double mu = hh * g * jl;
+  const bool act = traj >= 0;
+  if (act) {
+    if (c == 0) A.hhat[traj] = hh;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) A.acc_dp[((size_t)traj * D + c) * NP + q] = hh * g * Q[c * NP + q] * lam;
+    A.acc_dy0[(size_t)traj * D + c] = lam + mu;
+    A.phi0c[(size_t)traj * D + c] = wc[N - 1] * lam;
+  }
+  A.X[A.atiles[2 * tile].f_off + col] = act ? mu : 0.0;
+  A.X[A.atiles[2 * tile + 1].f_off + col] = act ? lam : 0.0;
+}
+
+// Reverse steps for targets t = s..s+nb-1 (row t+1 of the histories),
+// forward index k = N_i - 1 - t.  One warp per state component, one lane per
+// trajectory; the components meet through shared memory for J^T phi and
+// J^T lambda.
+template <int SYS>
+__global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_near_kernel(AdjArgs A, long long s, int nb) {
+  using S = Sys<SYS>;
+  constexpr int D = S::D, NP = S::NP, ld = kTrajPerTile * D;
+  extern __shared__ double adj_dyn[];
+  double (*Wm)[ld] = reinterpret_cast<double (*)[ld]>(adj_dyn);            // mu~ rows s..s+64
+  double (*Wl)[ld] = reinterpret_cast<double (*)[ld]>(adj_dyn + 65 * ld);  // lambda~ rows s..s+64
+  __shared__ double wsb[65], wsa[65];
+  __shared__ double xsh[D][32];
+  const int tile = blockIdx.x, c = threadIdx.x >> 5, lane = threadIdx.x & 31, col = lane * D + c;
+  const TileDesc& T = A.tiles[tile];
+  const int traj = T.traj[lane];
+  const int src = traj >= 0 ? traj : T.traj[0];
+  const double alpha = A.bucket_alpha[T.bucket];
+  const double* wb = A.bucket_b[T.bucket];
+  const double* wa = A.bucket_a[T.bucket];
+  const double* wc = A.bucket_c[T.bucket];
+  const double g = A.bucket_g[T.bucket];
+  const long long Ni = traj >= 0 ? (long long)A.N[traj] : -1;
+  const double h = A.h[src];
+  const double hh = traj >= 0 ? A.hhat[traj] : 0.0;
+  double p[kMaxParams];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) p[q] = A.params[(size_t)src * NP + q];
+  double* Xm = A.X + A.atiles[2 * tile].f_off;
+  double* Xl = A.X + A.atiles[2 * tile + 1].f_off;
+  for (int m = threadIdx.x; m < 65; m += 32 * D) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
+  Wm[0][col] = Xm[s * ld + col];
+  Wl[0][col] = Xl[s * ld + col];
+  double adp[NP], ady0 = 0.0, phc = 0.0;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) adp[q] = 0.0;
+  if (traj >= 0) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) adp[q] = A.acc_dp[((size_t)traj * D + c) * NP + q];
+    ady0 = A.acc_dy0[(size_t)traj * D + c];
+    phc = A.phi0c[(size_t)traj * D + c];
+  }
+  __syncthreads();
+  const size_t fstride = (size_t)A.far_tiles * 2 * A.B * ld;
+  for (int i = 0; i < nb; ++i) {
+    const long long t = s + i;
+    const long long k = Ni - 1 - t;  // forward index of this reverse step
+    const bool act = k >= 0;
+    const long long kk = act ? k : 0;
+    // inputs at k: y_k, y^P_k, G_k
+    double yk[D], ypk[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      yk[q] = A.Y[((size_t)src * A.ldY + kk) * D + q];
+      ypk[q] = A.YP[((size_t)src * A.ldY + kk) * D + q];
+    }
+    const double Gk = A.G[((size_t)src * A.ldY + kk) * D + c];
+    // far sums (mu~ rows through b, lambda~ rows through a)
+    double Sm = 0.0, Sl = 0.0;
+    if (s > 0) {
+      for (int q = 0; q < A.far_ksplit; ++q) {
+        Sm += A.far[q * fstride + ((((size_t)2 * tile) * 2 + 0) * A.B + i) * ld + col];
+        Sl += A.far[q * fstride + ((((size_t)2 * tile + 1) * 2 + 1) * A.B + i) * ld + col];
+      }
+    }
+    for (int r = 0; r <= i; ++r) {
+      Sm = fma(wsb[i - r], Wm[r][col], Sm);
+      Sl = fma(wsa[i - r], Wl[r][col], Sl);
+    }
+    const double phi = hh * (Sm + (k >= 1 ? Sl : phc));
+    xsh[c][lane] = phi;
+    bar_components<D>();
+    // Jacobians recomputed from the stored states: at y_k and at y^P_k
+    double Jy[D * D], Qy[D * NP], Jp[D * D], Qp[D * NP];
+    S::jac(p, alpha, (double)kk * h, yk, Jy, Qy);
+    S::jac(p, alpha, (double)kk * h, ypk, Jp, Qp);
+    double lam = Gk;
+#pragma unroll
+    for (int j = 0; j < D; ++j) lam = fma(Jy[j * D + c], xsh[j][lane], lam);
+    bar_components<D>();
+    xsh[c][lane] = lam;
+    bar_components<D>();
+    double jl = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) jl = fma(Jp[j * D + c], xsh[j][lane], jl);
+    bar_components<D>();
+    const double mu = hh * g * jl;
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) adp[q] = fma(Qy[c * NP + q], phi, adp[q]);
+      if (k >= 1) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) adp[q] = fma(hh * g * Qp[c * NP + q], lam, adp[q]);
+        ady0 += lam + mu;
+        phc = fma(wc[k - 1], lam, phc);
+      } else {  // k = 0: lambda here is G_0 + J_0^T phi_0
+        A.dy0[(size_t)traj * D + c] = ady0 + lam;
+      }
+      if (!(isfinite(lam) && isfinite(phi))) report_status(A.status, ABM_ERR_NONFINITE, traj, k);
+    }
+    const bool row = act && k >= 1;
+    Wm[i + 1][col] = row ? mu : 0.0;
+    Wl[i + 1][col] = row ? lam : 0.0;
+    Xm[(t + 1) * ld + col] = row ? mu : 0.0;
+    Xl[(t + 1) * ld + col] = row ? lam : 0.0;
+  }
+  if (traj >= 0) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) A.acc_dp[((size_t)traj * D + c) * NP + q] = adp[q];
+    A.acc_dy0[(size_t)traj * D + c] = ady0;
+    A.phi0c[(size_t)traj * D + c] = phc;
+  }
+  if (A.Xsh) {
+    __syncthreads();
+    // BF16 split rows s..s+63 of both histories, K-major 16-byte stores
+    constexpr int UNITS = 2 * 3 * ld * 8;
+    for (int u = threadIdx.x; u < UNITS; u += 32 * D) {
+      const int hist = u / (3 * ld * 8), rem0 = u % (3 * ld * 8);
+      const int pc = rem0 / (ld * 8), rem = rem0 % (ld * 8);
+      const int cc = rem / 8, part = rem % 8;
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        __nv_bfloat16 pcs[3];
+        split3_bf16_adj(hist == 0 ? Wm[part * 8 + r][cc] : Wl[part * 8 + r][cc], pcs);
+        v[r] = pcs[pc];
+      }
+      __nv_bfloat16* dst = A.Xsh + (size_t)pc * A.xsh_plane +
+                           ((size_t)(2 * tile + hist) * ld + cc) * A.xsh_ld + s + part * 8;
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+    }
+  }
+}
+
+template <int SYS>
+__global__ void adjoint_finish_kernel(AdjArgs A, int M) {
+  using S = Sys<SYS>;
+  constexpr int D = S::D, NP = S::NP;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * NP) return;
+  const int traj = idx / NP, q = idx % NP;
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) s += A.acc_dp[((size_t)traj * D + c) * NP + q];
+  A.dparams[(size_t)traj * NP + q] = s;
+}
+
+cudaError_t launch_adjoint_setup(int sys, const AdjArgs& A, int n_tiles, cudaStream_t st) {
+  ABM_DISPATCH_SYSTEM(sys, (adjoint_setup_kernel<SYS><<<n_tiles, 32 * Sys<SYS>::D, 0, st>>>(A)));
+  return cudaGetLastError();
+}
+
+template <int SYS>
+cudaError_t launch_adjoint_near_t(const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+  constexpr int D = Sys<SYS>::D;
+  const size_t smem = (size_t)2 * 65 * kTrajPerTile * D * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(adjoint_near_kernel<SYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  adjoint_near_kernel<SYS><<<n_active, 32 * D, smem, st>>>(A, s, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+  cudaError_t err = cudaErrorInvalidValue;
+  ABM_DISPATCH_SYSTEM(sys, err = (launch_adjoint_near_t<SYS>(A, n_active, s, nb, st)));
+  return err;
+}
+
+cudaError_t launch_adjoint_finish(int sys, const AdjArgs& A, int M, cudaStream_t st) {
+  ABM_DISPATCH_SYSTEM(sys, (adjoint_finish_kernel<SYS><<<(M * Sys<SYS>::NP + 255) / 256, 256, 0, st>>>(A, M)));
+  return cudaGetLastError();
+}
+
+}  // namespace abm

@@ -34,6 +34,9 @@ bool make_tmap_bf16(CUtensorMap* out, void* base, unsigned long long inner, unsi
 cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long ld, long long plane,
                             cudaStream_t st);
 cudaError_t launch_sum_partials(const double* far, int ksplit, int n_tiles, double* P, double* C, cudaStream_t st);
+cudaError_t launch_adjoint_setup(int sys, const AdjArgs& A, int n_tiles, cudaStream_t st);
+cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st);
+cudaError_t launch_adjoint_finish(int sys, const AdjArgs& A, int M, cudaStream_t st);
 }  // namespace abm
 
 using namespace abm;
@@ -96,6 +99,12 @@ struct abm_plan_s {
   long long Lbase = 0, Lx = 0;      // pre-expanded Toeplitz geometry
   CUtensorMap* d_tmapW = nullptr;   // [kMaxWeightSets][3]
   CUtensorMap* d_tmapF = nullptr;   // [3]
+  // adjoint workspace (allocated by the first abm_adjoint call)
+  double* Xadj = nullptr;           // FP64 mu~ / lambda~ histories, 2 tiles per forward tile
+  __nv_bfloat16* Xsh = nullptr;     // their BF16 split planes (tensor-core paths)
+  CUtensorMap* d_tmapX = nullptr;   // [3]
+  TileDesc* d_atiles = nullptr;     // [2 * max_tiles]
+  double *acc_dp = nullptr, *acc_dy0 = nullptr, *phi0c = nullptr;
   unsigned long long* status = nullptr;
   std::string err;
   // tracing: launches per kernel kind, optional event pairs around each launch
@@ -237,6 +246,104 @@ abm_status far_history_tc(abm_plan p, double alpha, const double* F, long long r
   return ABM_OK;
 }
 
+// Host-side scheduling shared by the batched solve and its adjoint: argument
+// checks, alpha groups (one weight set each), column tiles of 32 trajectories
+// ordered by N, history offsets, and the device tables the kernels read.
+struct Sched {
+  std::vector<double> ualpha;
+  std::vector<WeightSet*> ws;
+  std::vector<TileDesc> tiles;
+  int n_tiles = 0, nmax = 0, ksplit = 1;
+  size_t hist_elems = 0;
+};
+
+abm_status schedule_batch(abm_plan p, int M, const double* alpha, const double* h, const int* N, long long ldY,
+                          cudaStream_t st, Sched& S, const char* who) {
+  const int B = p->B, d = p->d;
+  int& nmax = S.nmax;
+  nmax = 0;
+  for (int i = 0; i < M; ++i) {
+    if (!alpha_ok(alpha[i]) || !(std::isfinite(h[i]) && h[i] > 0.0) || N[i] < 1 || N[i] > p->o.n_max)
+      return fail(p, ABM_ERR_INVALID_ARG, std::string(who) + ": trajectory " + std::to_string(i) +
+                                              " needs alpha in (0,1], finite h > 0, 1 <= N <= n_max");
+    nmax = std::max(nmax, N[i]);
+  }
+  if (ldY < (long long)nmax + 1) return fail(p, ABM_ERR_INVALID_ARG, std::string(who) + ": ldY < max(N)+1");
+  // ---- alpha groups ----
+  std::vector<double>& ualpha = S.ualpha;
+  for (int i = 0; i < M; ++i)
+    if (std::find(ualpha.begin(), ualpha.end(), alpha[i]) == ualpha.end()) ualpha.push_back(alpha[i]);
+  if ((int)ualpha.size() > kMaxWeightSets)
+    return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": more distinct alpha values than weight sets");
+  std::vector<WeightSet*>& ws = S.ws;
+  ws.assign(ualpha.size(), nullptr);
+  for (size_t g = 0; g < ualpha.size(); ++g) {
+    abm_status rs = get_weights(p, ualpha[g], st, &ws[g]);
+    if (rs) return rs;
+  }
+  // ---- column tiles: per group, ordered by N descending, 32 trajectories each ----
+  std::vector<TileDesc>& tiles = S.tiles;
+  tiles.clear();
+  for (size_t g = 0; g < ualpha.size(); ++g) {
+    std::vector<int> idx;
+    for (int i = 0; i < M; ++i)
+      if (alpha[i] == ualpha[g]) idx.push_back(i);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return N[x] > N[y]; });
+    for (size_t q = 0; q < idx.size(); q += kTrajPerTile) {
+      TileDesc t{};
+      for (int l = 0; l < kTrajPerTile; ++l) t.traj[l] = (q + l < idx.size()) ? idx[q + l] : -1;
+      t.bucket = (int)g;
+      t.n_tile = N[idx[q]];
+      tiles.push_back(t);
+    }
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const TileDesc& x, const TileDesc& y) { return x.n_tile > y.n_tile; });
+  if ((int)tiles.size() > p->max_tiles)
+    return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": too many column tiles for this plan");
+  size_t off = 0;
+  for (auto& t : tiles) {
+    t.f_off = (long long)off;
+    long long rows = (long long)((t.n_tile + B - 1) / B) * B + 1;
+    off += (size_t)rows * kTrajPerTile * d;
+  }
+  if (off > p->fb_cap) return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": history exceeds workspace");
+  const int n_tiles = (int)tiles.size();
+  S.n_tiles = n_tiles;
+  S.hist_elems = off;
+  if (p->Fsh && n_tiles > p->max_tiles) return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": too many tiles");
+  int& ksplit = S.ksplit;
+  ksplit = std::max(1, std::min(16, (2 * p->sms + n_tiles - 1) / n_tiles));
+  while ((size_t)ksplit * n_tiles * 2 * B * kTrajPerTile * d > p->farb_cap && ksplit > 1) --ksplit;
+  // ---- device tables ----
+  std::vector<double> balpha(ualpha), bg(ualpha.size());
+  std::vector<const double*> bptr(3 * kMaxWeightSets, nullptr);
+  std::vector<const float*> b32ptr(2 * kMaxWeightSets, nullptr);
+  for (size_t g = 0; g < ualpha.size(); ++g) {
+    bptr[g] = ws[g]->b;
+    bptr[kMaxWeightSets + g] = ws[g]->a;
+    bptr[2 * kMaxWeightSets + g] = ws[g]->c;
+    b32ptr[g] = ws[g]->b32;
+    b32ptr[kMaxWeightSets + g] = ws[g]->a32;
+    CK(cudaMemcpyAsync(p->d_bg + g, ws[g]->g, sizeof(double), cudaMemcpyDeviceToDevice, st), "g copy");
+  }
+  CK(cudaMemcpyAsync(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st), "tiles");
+  CK(cudaMemcpyAsync(p->d_h, h, M * sizeof(double), cudaMemcpyHostToDevice, st), "h");
+  CK(cudaMemcpyAsync(p->d_N, N, M * sizeof(int), cudaMemcpyHostToDevice, st), "N");
+  CK(cudaMemcpyAsync(p->d_balpha, balpha.data(), balpha.size() * sizeof(double), cudaMemcpyHostToDevice, st), "alpha");
+  CK(cudaMemcpyAsync(p->d_bptr, bptr.data(), bptr.size() * sizeof(double*), cudaMemcpyHostToDevice, st), "ptrs");
+  CK(cudaMemcpyAsync(p->d_b32ptr, b32ptr.data(), b32ptr.size() * sizeof(float*), cudaMemcpyHostToDevice, st), "ptrs");
+  if (p->Fsh) {
+    std::vector<CUtensorMap> mw(ualpha.size() * 3);
+    for (size_t g = 0; g < ualpha.size(); ++g)
+      for (int q = 0; q < 3; ++q)
+        if (!make_tmap_bf16(&mw[g * 3 + q], ws[g]->Wx + (size_t)q * 128 * p->Lx, (unsigned long long)p->Lx, 128,
+                            128))
+          return fail(p, ABM_ERR_CUDA, std::string(who) + ": tensor map of the Toeplitz pieces");
+    CK(cudaMemcpyAsync(p->d_tmapW, mw.data(), mw.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st), "tmaps");
+  }
+  return ABM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -309,7 +416,7 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
     p->max_tiles = (o->max_batch + kTrajPerTile - 1) / kTrajPerTile + kMaxWeightSets;
     p->max_tiles = std::min(p->max_tiles, o->max_batch);
     p->fb_cap = (size_t)p->max_tiles * rows * kTrajPerTile * d;
-    size_t far_units = (size_t)p->max_tiles + 2 * (size_t)p->sms + 16;
+    size_t far_units = 2 * (size_t)p->max_tiles + 2 * (size_t)p->sms + 16;  // adjoint: 2 tiles per tile
     p->farb_cap = far_units * 2 * B * kTrajPerTile * d;
     if (!alloc((void**)&p->Fb, p->fb_cap * sizeof(double)) ||
         (o->prec == ABM_PREC_FP32_FAR && !alloc((void**)&p->Fb32, p->fb_cap * sizeof(float))) ||
@@ -353,6 +460,8 @@ abm_status abm_plan_destroy(abm_plan p) {
     cudaFree(w.b); cudaFree(w.a); cudaFree(w.c); cudaFree(w.g); cudaFree(w.b32); cudaFree(w.a32); cudaFree(w.Wx);
   }
   cudaFree(p->Fsh); cudaFree(p->d_tmapW); cudaFree(p->d_tmapF);
+  cudaFree(p->Xadj); cudaFree(p->Xsh); cudaFree(p->d_tmapX); cudaFree(p->d_atiles);
+  cudaFree(p->acc_dp); cudaFree(p->acc_dy0); cudaFree(p->phi0c);
   cudaFree(p->ppartial); cudaFree(p->pflags);
   cudaFree(p->F1); cudaFree(p->far1); cudaFree(p->part1); cudaFree(p->tickets); cudaFree(p->hhat1);
   cudaFree(p->Fb); cudaFree(p->Fb32); cudaFree(p->farb); cudaFree(p->d_tiles); cudaFree(p->d_h);
@@ -477,89 +586,20 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
   if (!p) return ABM_ERR_INVALID_ARG;
   if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y)
     return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: need 1 <= M <= max_batch and non-null arrays");
-  int nmax = 0;
-  for (int i = 0; i < M; ++i) {
-    if (!alpha_ok(alpha[i]) || !(std::isfinite(h[i]) && h[i] > 0.0) || N[i] < 1 || N[i] > p->o.n_max)
-      return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: trajectory " + std::to_string(i) +
-                                              " needs alpha in (0,1], finite h > 0, 1 <= N <= n_max");
-    nmax = std::max(nmax, N[i]);
-  }
-  if (ldY < (long long)nmax + 1) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: ldY < max(N)+1");
   cudaStream_t st = (cudaStream_t)stream;
   const int B = p->B, d = p->d;
-  // ---- alpha groups ----
-  std::vector<double> ualpha;
-  for (int i = 0; i < M; ++i)
-    if (std::find(ualpha.begin(), ualpha.end(), alpha[i]) == ualpha.end()) ualpha.push_back(alpha[i]);
-  if ((int)ualpha.size() > kMaxWeightSets)
-    return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: more distinct alpha values than weight sets");
-  std::vector<WeightSet*> ws(ualpha.size());
-  for (size_t g = 0; g < ualpha.size(); ++g) {
-    abm_status rs = get_weights(p, ualpha[g], st, &ws[g]);
-    if (rs) return rs;
-  }
-  // ---- column tiles: per group, ordered by N descending, 32 trajectories each ----
-  std::vector<TileDesc> tiles;
-  for (size_t g = 0; g < ualpha.size(); ++g) {
-    std::vector<int> idx;
-    for (int i = 0; i < M; ++i)
-      if (alpha[i] == ualpha[g]) idx.push_back(i);
-    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return N[x] > N[y]; });
-    for (size_t q = 0; q < idx.size(); q += kTrajPerTile) {
-      TileDesc t{};
-      for (int l = 0; l < kTrajPerTile; ++l) t.traj[l] = (q + l < idx.size()) ? idx[q + l] : -1;
-      t.bucket = (int)g;
-      t.n_tile = N[idx[q]];
-      tiles.push_back(t);
-    }
-  }
-  std::stable_sort(tiles.begin(), tiles.end(), [](const TileDesc& x, const TileDesc& y) { return x.n_tile > y.n_tile; });
-  if ((int)tiles.size() > p->max_tiles)
-    return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: too many column tiles for this plan");
-  size_t off = 0;
-  for (auto& t : tiles) {
-    t.f_off = (long long)off;
-    long long rows = (long long)((t.n_tile + B - 1) / B) * B + 1;
-    off += (size_t)rows * kTrajPerTile * d;
-  }
-  if (off > p->fb_cap) return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: history exceeds workspace");
-  const int n_tiles = (int)tiles.size();
-  if (p->Fsh && n_tiles > p->max_tiles) return fail(p, ABM_ERR_UNSUPPORTED, "abm_solve_batched: too many tiles");
-  int ksplit = std::max(1, std::min(16, (2 * p->sms + n_tiles - 1) / n_tiles));
-  while ((size_t)ksplit * n_tiles * 2 * B * kTrajPerTile * d > p->farb_cap && ksplit > 1) --ksplit;
-  // ---- device tables ----
-  std::vector<double> balpha(ualpha), bg(ualpha.size());
-  std::vector<const double*> bptr(3 * kMaxWeightSets, nullptr);
-  std::vector<const float*> b32ptr(2 * kMaxWeightSets, nullptr);
-  for (size_t g = 0; g < ualpha.size(); ++g) {
-    bptr[g] = ws[g]->b;
-    bptr[kMaxWeightSets + g] = ws[g]->a;
-    bptr[2 * kMaxWeightSets + g] = ws[g]->c;
-    b32ptr[g] = ws[g]->b32;
-    b32ptr[kMaxWeightSets + g] = ws[g]->a32;
-    CK(cudaMemcpyAsync(p->d_bg + g, ws[g]->g, sizeof(double), cudaMemcpyDeviceToDevice, st), "g copy");
-  }
-  CK(cudaMemcpyAsync(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st), "tiles");
-  CK(cudaMemcpyAsync(p->d_h, h, M * sizeof(double), cudaMemcpyHostToDevice, st), "h");
-  CK(cudaMemcpyAsync(p->d_N, N, M * sizeof(int), cudaMemcpyHostToDevice, st), "N");
-  CK(cudaMemcpyAsync(p->d_balpha, balpha.data(), balpha.size() * sizeof(double), cudaMemcpyHostToDevice, st), "alpha");
-  CK(cudaMemcpyAsync(p->d_bptr, bptr.data(), bptr.size() * sizeof(double*), cudaMemcpyHostToDevice, st), "ptrs");
-  CK(cudaMemcpyAsync(p->d_b32ptr, b32ptr.data(), b32ptr.size() * sizeof(float*), cudaMemcpyHostToDevice, st), "ptrs");
+  Sched S;
+  abm_status rs = schedule_batch(p, M, alpha, h, N, ldY, st, S, "abm_solve_batched");
+  if (rs) return rs;
+  const int n_tiles = S.n_tiles, nmax = S.nmax, ksplit = S.ksplit;
+  const std::vector<TileDesc>& tiles = S.tiles;
   const bool tc_prec = p->Fsh != nullptr;
-  if (tc_prec) {
-    std::vector<CUtensorMap> mw(ualpha.size() * 3);
-    for (size_t g = 0; g < ualpha.size(); ++g)
-      for (int q = 0; q < 3; ++q)
-        if (!make_tmap_bf16(&mw[g * 3 + q], ws[g]->Wx + (size_t)q * 128 * p->Lx, (unsigned long long)p->Lx, 128,
-                            128))
-          return fail(p, ABM_ERR_CUDA, "abm_solve_batched: tensor map of the Toeplitz pieces");
-    CK(cudaMemcpyAsync(p->d_tmapW, mw.data(), mw.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st), "tmaps");
-  }
   BatchArgs A{};
   A.tiles = p->d_tiles;
   A.n_tiles = n_tiles;
   A.B = B;
   A.ksplit = ksplit;
+  A.far_k0 = 1;
   A.bucket_alpha = p->d_balpha;
   A.bucket_b = p->d_bptr;
   A.bucket_a = p->d_bptr + kMaxWeightSets;
@@ -652,10 +692,134 @@ abm_status abm_plan_kernel_times(abm_plan p, abm_kernel_kind kind, void* stream,
   return ABM_OK;
 }
 
-abm_status abm_adjoint(abm_plan p, int, const double*, const double*, const int*, const double*, const double*,
-                       const double*, const double*, long long, const double*, double*, double*, void*) {
+abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, const int* N, const double* params,
+                       const double* y0, const double* Y, const double* YP, long long ldY, const double* dLdY,
+                       double* dparams, double* dy0, void* stream) {
   if (!p) return ABM_ERR_INVALID_ARG;
-  return fail(p, ABM_ERR_UNSUPPORTED, "abm_adjoint: not built yet");
+  if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y || !YP || !dLdY || !dparams || !dy0)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_adjoint: need 1 <= M <= max_batch and non-null arrays (Y and YP too)");
+  if (p->o.prec == ABM_PREC_FP32_FAR)
+    return fail(p, ABM_ERR_UNSUPPORTED, "abm_adjoint: FP64 or tensor-core (BF16X3/X6) plans only");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = p->B, d = p->d;
+  Sched S;
+  abm_status rs = schedule_batch(p, M, alpha, h, N, ldY, st, S, "abm_adjoint");
+  if (rs) return rs;
+  const int n_tiles = S.n_tiles;
+  const bool tc_prec = p->Fsh != nullptr;
+  // ---- adjoint workspace ----
+  const size_t gcols = (size_t)2 * p->max_tiles * kTrajPerTile * d;
+  if (!p->Xadj) {
+    CK(cudaMalloc(&p->Xadj, 2 * p->fb_cap * sizeof(double)), "adjoint histories");
+    CK(cudaMalloc(&p->d_atiles, (size_t)2 * p->max_tiles * sizeof(TileDesc)), "adjoint tiles");
+    CK(cudaMalloc(&p->acc_dp, (size_t)p->o.max_batch * kMaxD * kMaxParams * sizeof(double)), "adjoint sums");
+    CK(cudaMalloc(&p->acc_dy0, (size_t)p->o.max_batch * kMaxD * sizeof(double)), "adjoint sums");
+    CK(cudaMalloc(&p->phi0c, (size_t)p->o.max_batch * kMaxD * sizeof(double)), "adjoint sums");
+    if (tc_prec) {
+      CK(cudaMalloc(&p->Xsh, 3 * gcols * p->fsh_ld * sizeof(__nv_bfloat16)), "adjoint planes");
+      CK(cudaMalloc(&p->d_tmapX, 3 * sizeof(CUtensorMap)), "adjoint tensor maps");
+      CUtensorMap mx[3];
+      for (int q = 0; q < 3; ++q)
+        if (!make_tmap_bf16(&mx[q], p->Xsh + (size_t)q * gcols * p->fsh_ld, (unsigned long long)p->fsh_ld, gcols,
+                            (unsigned)(kTrajPerTile * d)))
+          return fail(p, ABM_ERR_CUDA, "abm_adjoint: tensor map of the adjoint planes");
+      CK(cudaMemcpy(p->d_tmapX, mx, sizeof(mx), cudaMemcpyHostToDevice), "adjoint tensor maps");
+    }
+  }
+  // two adjoint tiles (mu~, lambda~) per forward tile, same trajectories and group
+  std::vector<TileDesc> at(2 * n_tiles);
+  size_t off = 0;
+  for (int t = 0; t < n_tiles; ++t) {
+    const long long rows = (long long)((S.tiles[t].n_tile + B - 1) / B) * B + 1;
+    for (int hh = 0; hh < 2; ++hh) {
+      at[2 * t + hh] = S.tiles[t];
+      at[2 * t + hh].f_off = (long long)off;
+      off += (size_t)rows * kTrajPerTile * d;
+    }
+  }
+  CK(cudaMemcpyAsync(p->d_atiles, at.data(), at.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st), "adjoint tiles");
+  AdjArgs A{};
+  A.tiles = p->d_tiles;
+  A.atiles = p->d_atiles;
+  A.B = B;
+  A.bucket_alpha = p->d_balpha;
+  A.bucket_b = p->d_bptr;
+  A.bucket_a = p->d_bptr + kMaxWeightSets;
+  A.bucket_c = p->d_bptr + 2 * kMaxWeightSets;
+  A.bucket_g = p->d_bg;
+  A.h = p->d_h;
+  A.N = p->d_N;
+  A.params = params;
+  A.y0 = y0;
+  A.hhat = p->d_hhat;
+  A.Y = Y;
+  A.YP = YP;
+  A.G = dLdY;
+  A.ldY = ldY;
+  A.X = p->Xadj;
+  A.Xsh = p->Xsh;
+  A.xsh_ld = p->fsh_ld;
+  A.xsh_plane = (long long)gcols * p->fsh_ld;
+  A.far = p->farb;
+  A.acc_dp = p->acc_dp;
+  A.acc_dy0 = p->acc_dy0;
+  A.phi0c = p->phi0c;
+  A.dparams = dparams;
+  A.dy0 = dy0;
+  A.status = p->status;
+  {
+    Trace tr(p, ABM_KERNEL_ADJOINT, st);
+    CK(launch_adjoint_setup(p->sys, A, n_tiles, st), "adjoint setup kernel");
+  }
+  // FP64 far sums of the adjoint histories reuse the batched FP64 far kernel
+  BatchArgs F{};
+  F.tiles = p->d_atiles;
+  F.B = B;
+  F.far_k0 = 0;  // reversed row 0 (the k = N terms) is an ordinary row here
+  F.bucket_alpha = p->d_balpha;
+  F.bucket_b = p->d_bptr;
+  F.bucket_a = p->d_bptr + kMaxWeightSets;
+  F.bucket_c = p->d_bptr + 2 * kMaxWeightSets;
+  F.bucket_g = p->d_bg;
+  F.F = p->Xadj;
+  F.far = p->farb;
+  F.status = p->status;
+  const int ntime = (S.nmax + B - 1) / B;
+  int n_active = n_tiles;
+  for (int j = 0; j < ntime; ++j) {
+    const long long s = (long long)j * B;
+    while (n_active > 0 && S.tiles[n_active - 1].n_tile <= s) --n_active;
+    if (n_active == 0) break;
+    const int na2 = 2 * n_active;
+    A.far_tiles = na2;
+    A.far_ksplit = 1;
+    if (s > 0) {
+      if (tc_prec) {
+        const int nkb_total = (int)(s / 64);
+        const int ks = std::max(1, std::min(nkb_total, (2 * p->sms + na2 - 1) / na2));
+        CK(cudaMemsetAsync(p->farb, 0, (size_t)na2 * 2 * B * kTrajPerTile * d * sizeof(double), st), "far sums reset");
+        FarTcArgs T{p->d_atiles, p->d_tmapW, p->d_tmapX, p->farb, p->status, s, p->Lbase,
+                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, na2, ks};
+        Trace tr(p, ABM_KERNEL_ADJOINT, st);
+        CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, na2, st), "adjoint tensor-core far kernel");
+      } else {
+        int ks = std::max(1, std::min(16, (2 * p->sms + na2 - 1) / na2));
+        while ((size_t)ks * na2 * 2 * B * kTrajPerTile * d > p->farb_cap && ks > 1) --ks;
+        F.n_tiles = na2;
+        F.ksplit = ks;
+        A.far_ksplit = ks;
+        Trace tr(p, ABM_KERNEL_ADJOINT, st);
+        CK(launch_batched_far(d, ABM_PREC_FP64, F, na2, s, st), "adjoint far kernel");
+      }
+    }
+    Trace tr(p, ABM_KERNEL_ADJOINT, st);
+    CK(launch_adjoint_near(p->sys, A, n_active, s, B, st), "adjoint near kernel");
+  }
+  {
+    Trace tr(p, ABM_KERNEL_ADJOINT, st);
+    CK(launch_adjoint_finish(p->sys, A, M, st), "adjoint finish kernel");
+  }
+  return ABM_OK;
 }
 
 }  // extern "C"

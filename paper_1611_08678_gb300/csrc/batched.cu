@@ -235,9 +235,9 @@ __global__ void __launch_bounds__(256) batched_far_fp64_kernel(BatchArgs A, long
   const double* __restrict__ wa = A.bucket_a[T.bucket];
   const double* __restrict__ F = A.F + T.f_off;
   // history rows [1, s) split into ksplit chunks
-  const long long K = s - 1;
+  const long long K = s - A.far_k0;
   const long long chunk = (K + A.ksplit - 1) / A.ksplit;
-  const long long kb = 1 + (long long)q * chunk, ke = min(s, kb + chunk);
+  const long long kb = A.far_k0 + (long long)q * chunk, ke = min(s, kb + chunk);
   const int i0 = warp * R;
   double accP[R][D], accC[R][D];
 #pragma unroll
@@ -287,9 +287,9 @@ __global__ void __launch_bounds__(512) batched_far_fp32_kernel(BatchArgs A, long
   const float* __restrict__ wb = A.bucket_b32[T.bucket];
   const float* __restrict__ wa = A.bucket_a32[T.bucket];
   const float* __restrict__ F = A.F32 + T.f_off;
-  const long long K = s - 1;
+  const long long K = s - A.far_k0;
   const long long chunk = (K + A.ksplit - 1) / A.ksplit;
-  const long long kb = 1 + (long long)q * chunk, ke = min(s, kb + chunk);
+  const long long kb = A.far_k0 + (long long)q * chunk, ke = min(s, kb + chunk);
   const int i0 = warp * R;
   double dP[R][D], dC[R][D];
 #pragma unroll

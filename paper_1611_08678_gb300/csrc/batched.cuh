@@ -21,6 +21,8 @@ struct BatchArgs {
   int n_tiles;
   int B;                   // time-tile length
   int ksplit;              // history split of the far kernel
+  int far_k0;              // first history row of the far sums: 1 forward (row 0 = the
+                           // j = 0 term, kept in FP64), 0 adjoint
   // per alpha group
   const double* bucket_alpha;
   const double* const* bucket_b;
@@ -62,6 +64,38 @@ struct FarTcArgs {
   long long budget;          // clock cycles per bounded wait
   int n_tiles;
   int ksplit;
+};
+
+// Arguments of the adjoint kernels (adjoint.cu).
+struct AdjArgs {
+  const TileDesc* tiles;   // forward column tiles (sorted by n_tile descending)
+  const TileDesc* atiles;  // adjoint tiles: 2t = mu~ history, 2t+1 = lambda~ history
+  int B;
+  const double* bucket_alpha;
+  const double* const* bucket_b;
+  const double* const* bucket_a;
+  const double* const* bucket_c;
+  const double* bucket_g;
+  const double* h;
+  const int* N;
+  const double* params;
+  const double* y0;
+  double* hhat;
+  const double* Y;
+  const double* YP;
+  const double* G;
+  long long ldY;
+  double* X;               // FP64 adjoint histories, tile t at atiles[t].f_off, [rows][32*D]
+  __nv_bfloat16* Xsh;      // BF16 split planes of the adjoint histories (tensor paths) or null
+  long long xsh_ld, xsh_plane;
+  const double* far;       // far sums: [ksplit][far_tiles][2][B][32*D]
+  int far_ksplit, far_tiles;
+  double* acc_dp;          // [M][D][NP]
+  double* acc_dy0;         // [M][D]
+  double* phi0c;           // [M][D] running sum_n c_{n-1} lambda_n
+  double* dparams;         // [M][NP] (written by the finish kernel)
+  double* dy0;             // [M][D]
+  unsigned long long* status;
 };
 
 }  // namespace abm
