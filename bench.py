@@ -65,10 +65,12 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="chen_single",
-                    choices=["chen_single", "lorenz_single", "rossler_batched", "financial_batched"])
+                    choices=["chen_single", "lorenz_single", "rossler_batched", "financial_batched",
+                             "lorenz_adjoint"])
     ap.add_argument("--prec", default=None, help="far-history precision of batched workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mib", type=int, default=256)
+    ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner (library defaults)")
     return ap.parse_args(argv)
 
 
@@ -83,6 +85,8 @@ def workload(name):
         return wl.rossler_batched(), "bf16x6"
     if name == "financial_batched":
         return wl.financial_batched(), "bf16x6"
+    if name == "lorenz_adjoint":
+        return wl.lorenz_adjoint()[0], "bf16x6"
     raise ValueError(name)
 
 
@@ -281,6 +285,14 @@ def bench_single(args, name, w, world, rank, local):
     return out
 
 
+def shard_indices(M, rank, world, N=None):
+    """Trajectories of one rank: round-robin over the trajectories ordered by
+    N (descending), so every rank gets a similar share of the O(N^2) work."""
+    import numpy as np
+    order = np.argsort(-np.asarray(N), kind="stable") if N is not None else np.arange(M)
+    return np.sort(order[rank::world])
+
+
 def tile_schedule(w, per_tile=32):
     """Column tiles the library forms (alpha groups, N descending, 32 per tile):
     list of (n_tile, bucket, N of its trajectories)."""
@@ -325,10 +337,15 @@ def bench_batched(args, name, w, prec, world, rank, local):
     import torch
 
     from paper_1611_08678_gb300 import abm
-    shard = w.subset(np.arange(rank, w.M, world)) if world > 1 else w
+    shard = w.subset(shard_indices(w.M, rank, world, w.N)) if world > 1 else w
     N = shard.N
     ldY = int(N.max()) + 1
-    plan = abm.Plan(shard.system, n_max=int(N.max()), max_batch=shard.M, prec=prec, profile=True)
+    tuned = {"near_warps": 0, "far_split": 0}
+    if prec.startswith("bf16") and not args.no_tune:
+        from paper_1611_08678_gb300 import autotune
+        tuned = autotune.tune_batched(shard, prec)  # untimed; cached per shape
+    plan = abm.Plan(shard.system, n_max=int(N.max()), max_batch=shard.M, prec=prec, profile=True,
+                    near_warps=tuned["near_warps"], far_split=tuned["far_split"])
     params = torch.as_tensor(shard.params, device="cuda")
     y0 = torch.as_tensor(shard.y0, device="cuda")
     Y = torch.empty(shard.M, ldY, shard.d, dtype=torch.float64, device="cuda")
@@ -416,6 +433,8 @@ def bench_batched(args, name, w, prec, world, rank, local):
                    "N_range": [int(w.N.min()), int(w.N.max())], "sum_N": int(w.N.sum()),
                    "alphas": sorted(set(float(a) for a in w.alpha)), "far_precision": prec,
                    "parallelism": f"trajectory shards x{world}",
+                   "tuned": {"near_warps": tuned["near_warps"], "far_split": tuned["far_split"],
+                             "cached": bool(tuned.get("cached", False))},
                    "l2": "inputs larger than L2 (f history of all trajectories, several GB)"},
         "history_mac_per_s": macs_all / total_max,
         "roofline": roof,
@@ -467,6 +486,117 @@ def batched_cpu_baseline(w, Y=None, n_sub=16):
     return out
 
 
+def bench_adjoint(args, name, prec, world, rank, local):
+    """Forward solve + loss partials + adjoint (dL/dparams, dL/dy0) per step:
+    1024 fractional Lorenz trajectories, N = 2^14, loss = mean squared distance
+    to the trajectories of perturbed parameters."""
+    import numpy as np
+    import torch
+
+    from paper_1611_08678_gb300 import abm, workloads
+    w_all, tparams_all = workloads.lorenz_adjoint()
+    idx = shard_indices(w_all.M, rank, world, w_all.N) if world > 1 else np.arange(w_all.M)
+    w, tparams = w_all.subset(idx), tparams_all[idx]
+    N, M, d = int(w.N.max()), w.M, w.d
+    plan = abm.Plan("lorenz", n_max=N, max_batch=M, prec=prec, profile=True)
+    params = torch.as_tensor(w.params, device="cuda")
+    y0 = torch.as_tensor(w.y0, device="cuda")
+    Y = torch.zeros(M, N + 1, d, dtype=torch.float64, device="cuda")
+    YP = torch.zeros_like(Y)
+    Yt = plan.solve_batched(w.alpha, w.h, w.N, torch.as_tensor(tparams, device="cuda"), y0)  # targets
+    scale = 2.0 / ((N + 1) * d)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.solve_batched(w.alpha, w.h, w.N, params, y0, Y=Y, YP=YP, sync=False, stream=stream)
+        G = (Y - Yt) * scale
+        return plan.adjoint(w.alpha, w.h, w.N, params, y0, Y, YP, G, sync=False, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    plan.sync(stream)
+    for k in abm.KERNEL_KINDS:
+        plan.kernel_times(k, reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        dp, dy0 = step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    plan.sync(stream)
+    times = {k: plan.kernel_times(k, reset=True) for k in abm.KERNEL_KINDS}
+    total = sum(a.elapsed_time(b) / 1e3 for a, b in ev)
+    t = torch.tensor([total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = float(w_all.N.sum()) * args.steps / total_max
+    nprod = 3 if prec == "bf16x3" else 6
+    far_n, far_ms = times["far"]
+    alg, raw, byts = far_work(w, nprod)
+    far_sec = far_ms / 1e3 / args.steps
+    out = {
+        "metric": "trajectory-steps/s of forward + adjoint (history MAC/s beside; gradient error vs oracle stated)",
+        "value": value, "unit": "trajectory-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": f"f64 state, {prec} far", "data": "synthetic",
+        "config": {"workload": name, "system": "lorenz", "trajectories": int(w_all.M), "N": N,
+                   "far_precision": prec, "parallelism": f"trajectory shards x{world}",
+                   "l2": "inputs larger than L2 (histories of 1024 trajectories, several GB)"},
+        "history_mac_per_s": 2 * w_all.history_macs() * args.steps / total_max,
+        "roofline": {"bound": "hbm", "achieved": byts / far_sec / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                     "frac": byts / far_sec / 1e9 / HBM_PEAK_GBS, "traffic": None,
+                     "kernel": f"far_tc_kernel<{nprod}> (forward launches)",
+                     "tensor_tflops_raw": raw / far_sec / 1e12, "tensor_frac": raw / far_sec / 1e12 / BF16_PEAK_TFLOPS},
+        "kernel_ms_per_solve": {k: v[1] / args.steps for k, v in times.items() if v[0]},
+        "gpu_launches": int(sum(v[0] for v in times.values())),
+        "clocks": clk,
+    }
+    # e2e: inputs from pinned host memory, gradients back to the host
+    p_host = torch.as_tensor(w.params).pin_memory()
+    y_host = torch.as_tensor(w.y0).pin_memory()
+    dp_h = torch.empty(M, 3, dtype=torch.float64, pin_memory=True)
+    dy_h = torch.empty(M, d, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(2):
+        params.copy_(p_host, non_blocking=True)
+        y0.copy_(y_host, non_blocking=True)
+        dp, dy0 = step()
+        dp_h.copy_(dp, non_blocking=True)
+        dy_h.copy_(dy0, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["e2e"] = {"value": float(w.N.sum()) * 2 * world / (e0.elapsed_time(e1) / 1e3), "unit": "trajectory-steps/s",
+                  "h2d_bytes_per_step": int((p_host.numel() + y_host.numel()) * 8),
+                  "d2h_bytes_per_step": int((dp_h.numel() + dy_h.numel()) * 8)}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        Yn, Ytn = Y.cpu().numpy(), Yt.cpu().numpy()
+        dpn, dyn = dp.cpu().numpy(), dy0.cpu().numpy()
+        errs, t0 = [], time.perf_counter()
+        for i in (0, M - 1):
+            Gi = (Yn[i] - Ytn[i]) * scale
+            op, oy = oracle.tangent("lorenz", float(w.alpha[i]), float(w.h[i]), N, w.params[i], w.y0[i], Gi)
+            errs.append(max(np.max(np.abs(dpn[i] - op)) / np.max(np.abs(op)),
+                            np.max(np.abs(dyn[i] - oy)) / np.max(np.abs(oy))))
+        sec = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 2 * N / sec, "unit": "trajectory-steps/s", "cores": 1, "kind": "oracle",
+                               "sample": f"tangent-linear gradient of 2 trajectories ({sec:.1f} s, 1 host thread)"}
+        out["max_rel_err_vs_oracle"] = float(max(errs))
+        out["error_window"] = "gradients dL/dparams, dL/dy0 of 2 trajectories vs the oracle tangent-linear gradient"
+    return out
+
+
 def bench_reference(args, name, w, world, rank):
     """The oracle, as it stands, on the host cores: each step a bounded sample."""
     if rank != 0:
@@ -510,6 +640,8 @@ def main(argv=None):
         torch.distributed.init_process_group("nccl")
     if is_single(args.workload):
         out = bench_single(args, args.workload, w, world, rank, local)
+    elif args.workload == "lorenz_adjoint":
+        out = bench_adjoint(args, args.workload, prec, world, rank, local)
     else:
         out = bench_batched(args, args.workload, w, prec, world, rank, local)
     if rank == 0:

@@ -91,8 +91,11 @@ typedef struct {
   int max_batch;       /* largest M for abm_solve_batched (0: single only)       */
   int tile_B;          /* time-tile length B (0 = library default)               */
   int far_ctas;        /* CTAs of the single-trajectory far kernel (0 = auto)    */
-  int use_graph;       /* 1: capture the launch sequence in a CUDA graph and
-                          replay it while the arguments' shapes are unchanged    */
+  int use_graph;       /* batched solve: 1 = capture the launch sequence in a
+                          CUDA graph on the first call and replay it on calls
+                          with identical arguments (same host arrays' values,
+                          same device pointers); profiling events are skipped
+                          inside the graph                                        */
   long long spin_timeout_cycles; /* bound of every device-side wait in clock
                           cycles (0 = default, about two seconds)                */
   int test_withhold_tile; /* testing only, 0 = off.  k > 0: in abm_solve the far
@@ -102,6 +105,8 @@ typedef struct {
                           launching stream (see abm_plan_kernel_times)           */
   int near_warps;      /* batched near kernel: warps per state component (lag
                           slices): 0 = chosen from the active tiles, or 1, 2, 4  */
+  int far_split;       /* tensor-core far kernel: CTAs per time tile in waves of
+                          the SM count (history split across CTAs); 0 = 2        */
   int reserved[8];     /* must be zero                                            */
 } abm_plan_opts;
 

@@ -105,6 +105,10 @@ struct abm_plan_s {
   CUtensorMap* d_tmapX = nullptr;   // [3]
   TileDesc* d_atiles = nullptr;     // [2 * max_tiles]
   double *acc_dp = nullptr, *acc_dy0 = nullptr, *phi0c = nullptr;
+  // CUDA graph of the batched launch sequence (opts.use_graph)
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
+  bool capturing = false;
   unsigned long long* status = nullptr;
   std::string err;
   // tracing: launches per kernel kind, optional event pairs around each launch
@@ -159,7 +163,7 @@ struct Trace {
   size_t idx = (size_t)-1;
   Trace(abm_plan p_, int kind_, cudaStream_t st_) : p(p_), kind(kind_), st(st_) {
     p->launches[kind] += 1;
-    if (!p->o.profile) return;
+    if (!p->o.profile || p->capturing) return;
     if (p->ev_used.size() >= p->ev_pool.size()) {
       cudaEvent_t a, b;
       if (cudaEventCreate(&a) != cudaSuccess) return;
@@ -344,6 +348,54 @@ abm_status schedule_batch(abm_plan p, int M, const double* alpha, const double* 
   return ABM_OK;
 }
 
+// The far / near launch sequence of one batched solve on stream st (tables
+// already on the device).
+abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t st) {
+  const int B = p->B, d = p->d;
+  const bool tc_prec = p->Fsh != nullptr;
+  const std::vector<TileDesc>& tiles = S.tiles;
+  CK(launch_batched_setup(p->sys, A, S.n_tiles, st), "setup kernel");
+  const int ntime = (S.nmax + B - 1) / B;
+  int n_active = S.n_tiles;
+  for (int j = 0; j < ntime; ++j) {
+    const long long s = (long long)j * B;
+    while (n_active > 0 && tiles[n_active - 1].n_tile <= s) --n_active;
+    if (n_active == 0) break;
+    A.n_tiles = n_active;  // far sums of this time tile: [ksplit][n_active][2][B][cols]
+    if (s > 1) {
+      if (tc_prec) {
+        const int nkb_total = (int)(s / 64);
+        const int waves = p->o.far_split > 0 ? p->o.far_split : 2;
+        const int ks = std::max(1, std::min(nkb_total, (waves * p->sms + n_active - 1) / n_active));
+        A.ksplit = 1;  // the K-split parts are added on the device
+        CK(cudaMemsetAsync(p->farb, 0, (size_t)n_active * 2 * B * kTrajPerTile * d * sizeof(double), st),
+           "far sums reset");
+        FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
+                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, n_active, ks};
+        Trace tr(p, ABM_KERNEL_FAR, st);
+        CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, n_active, st), "tensor-core far kernel");
+      } else {
+        Trace tr(p, ABM_KERNEL_FAR, st);
+        CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
+      }
+    }
+    {
+      Trace tr(p, ABM_KERNEL_NEAR, st);
+      // warps per component: latency when few tiles are active, throughput when many
+      const int qw = p->o.near_warps ? p->o.near_warps
+                                     : (n_active <= p->sms ? 4 : (n_active <= 2 * p->sms ? 2 : 1));
+      CK(launch_batched_near(p->sys, A, n_active, s, B, qw, st), "near kernel");
+    }
+  }
+  return ABM_OK;
+}
+
+template <typename T>
+void key_append(std::vector<unsigned char>& k, const T* v, size_t n) {
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(v);
+  k.insert(k.end(), b, b + n * sizeof(T));
+}
+
 }  // namespace
 
 extern "C" {
@@ -371,6 +423,7 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
   if (o->tile_B && o->tile_B != 64 && o->tile_B != 32) return ABM_ERR_UNSUPPORTED;
   if (o->near_warps != 0 && o->near_warps != 1 && o->near_warps != 2 && o->near_warps != 4)
     return ABM_ERR_INVALID_ARG;
+  if (o->far_split < 0 || o->far_split > 64) return ABM_ERR_INVALID_ARG;
   const bool tc_prec = o->prec == ABM_PREC_BF16X3_FAR || o->prec == ABM_PREC_BF16X6_FAR;
   if (tc_prec && (sys_dim(sys) != 3 || (o->tile_B && o->tile_B != 64))) return ABM_ERR_UNSUPPORTED;
   abm_plan p = new abm_plan_s();
@@ -462,6 +515,7 @@ abm_status abm_plan_destroy(abm_plan p) {
   cudaFree(p->Fsh); cudaFree(p->d_tmapW); cudaFree(p->d_tmapF);
   cudaFree(p->Xadj); cudaFree(p->Xsh); cudaFree(p->d_tmapX); cudaFree(p->d_atiles);
   cudaFree(p->acc_dp); cudaFree(p->acc_dy0); cudaFree(p->phi0c);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   cudaFree(p->ppartial); cudaFree(p->pflags);
   cudaFree(p->F1); cudaFree(p->far1); cudaFree(p->part1); cudaFree(p->tickets); cudaFree(p->hhat1);
   cudaFree(p->Fb); cudaFree(p->Fb32); cudaFree(p->farb); cudaFree(p->d_tiles); cudaFree(p->d_h);
@@ -587,18 +641,33 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
   if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y)
     return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: need 1 <= M <= max_batch and non-null arrays");
   cudaStream_t st = (cudaStream_t)stream;
+  // with use_graph, a call whose arguments equal those of the captured call
+  // replays the graph (the device tables it reads are still in place)
+  std::vector<unsigned char> key;
+  if (p->o.use_graph) {
+    key_append(key, &M, 1);
+    key_append(key, alpha, M);
+    key_append(key, h, M);
+    key_append(key, N, M);
+    const void* ptrs[5] = {params, y0, Y, YP, nullptr};
+    key_append(key, ptrs, 5);
+    key_append(key, &ldY, 1);
+    if (p->graph_exec && key == p->graph_key) {
+      for (int i = 0; i < M; ++i)  // the same host checks as an uncaptured call
+        if (!alpha_ok(alpha[i]) || N[i] < 1 || N[i] > p->o.n_max) return fail(p, ABM_ERR_INVALID_ARG, "bad args");
+      CK(cudaGraphLaunch(p->graph_exec, st), "graph launch");
+      return ABM_OK;
+    }
+  }
   const int B = p->B, d = p->d;
   Sched S;
   abm_status rs = schedule_batch(p, M, alpha, h, N, ldY, st, S, "abm_solve_batched");
   if (rs) return rs;
-  const int n_tiles = S.n_tiles, nmax = S.nmax, ksplit = S.ksplit;
-  const std::vector<TileDesc>& tiles = S.tiles;
-  const bool tc_prec = p->Fsh != nullptr;
   BatchArgs A{};
   A.tiles = p->d_tiles;
-  A.n_tiles = n_tiles;
+  A.n_tiles = S.n_tiles;
   A.B = B;
-  A.ksplit = ksplit;
+  A.ksplit = S.ksplit;
   A.far_k0 = 1;
   A.bucket_alpha = p->d_balpha;
   A.bucket_b = p->d_bptr;
@@ -622,38 +691,27 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
   A.YP = YP;
   A.ldY = ldY;
   A.status = p->status;
-  CK(launch_batched_setup(p->sys, A, n_tiles, st), "setup kernel");
-  const int ntime = (nmax + B - 1) / B;
-  int n_active = n_tiles;
-  for (int j = 0; j < ntime; ++j) {
-    const long long s = (long long)j * B;
-    while (n_active > 0 && tiles[n_active - 1].n_tile <= s) --n_active;
-    if (n_active == 0) break;
-    A.n_tiles = n_active;  // far partials of this time tile: [ksplit][n_active][2][B][cols]
-    if (s > 1) {
-      if (tc_prec) {
-        const int nkb_total = (int)(s / 64);
-        const int ks = std::max(1, std::min(nkb_total, (2 * p->sms + n_active - 1) / n_active));
-        A.ksplit = 1;  // the K-split parts are added on the device
-        CK(cudaMemsetAsync(p->farb, 0, (size_t)n_active * 2 * B * kTrajPerTile * d * sizeof(double), st),
-           "far sums reset");
-        FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
-                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, n_active, ks};
-        Trace tr(p, ABM_KERNEL_FAR, st);
-        CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, n_active, st), "tensor-core far kernel");
-      } else {
-        Trace tr(p, ABM_KERNEL_FAR, st);
-        CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
-      }
-    }
-    {
-      Trace tr(p, ABM_KERNEL_NEAR, st);
-      // warps per component: latency when few tiles are active, throughput when many
-      const int qw = p->o.near_warps ? p->o.near_warps
-                                     : (n_active <= p->sms ? 4 : (n_active <= 2 * p->sms ? 2 : 1));
-      CK(launch_batched_near(p->sys, A, n_active, s, B, qw, st), "near kernel");
-    }
+  if (!p->o.use_graph) return enqueue_batched(p, S, A, st);
+  // capture the launch sequence on the plan's side stream, after the uploads
+  if (p->graph_exec) {
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
   }
+  CK(cudaEventRecord(p->ev_start, st), "event");
+  CK(cudaStreamWaitEvent(p->side, p->ev_start, 0), "event wait");
+  CK(cudaStreamBeginCapture(p->side, cudaStreamCaptureModeThreadLocal), "begin capture");
+  p->capturing = true;
+  rs = enqueue_batched(p, S, A, p->side);
+  p->capturing = false;
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(p->side, &graph);
+  if (rs) { if (graph) cudaGraphDestroy(graph); return rs; }
+  if (ce != cudaSuccess) return cuda_fail(p, ce, "end capture");
+  ce = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) { p->graph_exec = nullptr; return cuda_fail(p, ce, "graph instantiate"); }
+  p->graph_key = key;
+  CK(cudaGraphLaunch(p->graph_exec, st), "graph launch");
   return ABM_OK;
 }
 

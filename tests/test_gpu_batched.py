@@ -135,3 +135,25 @@ def test_batched_tensor_core_error_reported(abm, prec, tol, system, alphas):
     errs = _errors(batch, Y, t_max=5.0)
     print(f"{system} {prec} max rel err (t<=5): {errs.max():.3e}")
     assert errs.max() <= tol
+
+
+def test_batched_graph_capture_replays_identically(abm):
+    """use_graph: the first call captures the launch sequence, an identical
+    call replays it; results equal an uncaptured plan's; changed arguments
+    re-capture."""
+    batch = workloads.random_batch("rossler", 70, 200, 700, [0.85, 0.95])
+    ref = abm.Plan("rossler", n_max=700, max_batch=70, prec="bf16x6")
+    Yr = ref.solve_batched(batch.alpha, batch.h, batch.N, batch.params, batch.y0).cpu().numpy()
+    g = abm.Plan("rossler", n_max=700, max_batch=70, prec="bf16x6", use_graph=True)
+    params = torch.as_tensor(batch.params, device="cuda")
+    y0 = torch.as_tensor(batch.y0, device="cuda")
+    Y = torch.zeros(70, 701, 3, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        Y.zero_()
+        g.solve_batched(batch.alpha, batch.h, batch.N, params, y0, Y=Y, ldY=701)
+        assert np.array_equal(Y.cpu().numpy(), Yr)
+    N2 = batch.N.copy()
+    N2[0] = 150
+    Y.zero_()
+    g.solve_batched(batch.alpha, batch.h, N2, params, y0, Y=Y, ldY=701)
+    assert np.array_equal(Y.cpu().numpy()[1:], Yr[1:]) and np.array_equal(Y.cpu().numpy()[0, :151], Yr[0, :151])
