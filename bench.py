@@ -71,6 +71,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mib", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner (library defaults)")
+    ap.add_argument("--trajectories", type=int, default=0,
+                    help="batched workloads: first M trajectories only (small cases for profiling)")
     return ap.parse_args(argv)
 
 
@@ -629,6 +631,9 @@ def main(argv=None):
     world, rank, local = dist_env()
     w, default_prec = workload(args.workload)
     prec = args.prec or default_prec
+    if args.trajectories and not is_single(args.workload) and args.workload != "lorenz_adjoint":
+        import numpy as np
+        w = w.subset(np.arange(min(args.trajectories, w.M)))
     if args.impl == "reference":
         out = bench_reference(args, args.workload, w, world, rank)
         if out is not None:
