@@ -103,8 +103,10 @@ typedef struct {
                           runs out and the call reports ABM_ERR_TIMEOUT           */
   int profile;         /* 1: bracket every kernel launch with CUDA events on the
                           launching stream (see abm_plan_kernel_times)           */
-  int near_warps;      /* batched near kernel: warps per state component (lag
-                          slices): 0 = chosen from the active tiles, or 1, 2, 4  */
+  int near_warps;      /* batched near kernel: warps per state component, the
+                          chain warp plus helpers that sum the next step's window
+                          (lag slices) while the chain runs: 0 = chosen from the
+                          active tiles, 1 (chain only), 2, 3 or 5                */
   int far_split;       /* tensor-core far kernel: CTAs per time tile in waves of
                           the SM count (history split across CTAs); 0 = 2        */
   int reserved[8];     /* must be zero                                            */

@@ -1,9 +1,10 @@
 """Autotuner of the batched path's launch shapes.
 
 The kernels expose two shape knobs (include/abm.h, abm_plan_opts):
-  near_warps : warps per state component in the near kernel (lag slices):
-               1, 2 or 4 - FP64 latency per step against throughput when many
-               column tiles share an SM
+  near_warps : warps per state component in the near kernel, the chain warp
+               plus helpers summing slices of the next step's window while the
+               chain runs: 1 (chain only), 2 or 3 - FP64 latency per step
+               against instruction count when many column tiles share an SM
   far_split  : CTAs of the tensor-core far kernel per time tile, in waves of
                the SM count (the history of each column tile is split across
                that many CTAs, their parts added on the device)
@@ -23,7 +24,7 @@ from typing import Callable, Dict, Iterable, List, Optional, Tuple
 import numpy as np
 
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = tuple(
-    (nw, fs) for nw in (1, 2, 4) for fs in (1, 2, 4))
+    (nw, fs) for nw in (1, 2, 3) for fs in (1, 2, 4))
 _lock = threading.Lock()
 
 

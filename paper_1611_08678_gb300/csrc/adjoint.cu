@@ -86,122 +86,202 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_setup_kernel(AdjArgs
 }
 
 // Reverse steps for targets t = s..s+nb-1 (row t+1 of the histories),
-// forward index k = N_i - 1 - t.  One warp per state component, one lane per
-// trajectory; the components meet through shared memory for J^T phi and
-// J^T lambda.
-template <int SYS>
-__global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_near_kernel(AdjArgs A, long long s, int nb) {
+// forward index k = N_i - 1 - t.  Chain warps (one per state component, one
+// lane per trajectory) run the reverse step; the components meet through
+// shared memory for J^T phi and J^T lambda.  As in the forward near kernel,
+// HS helper warps per component sum step i+1's window over the rows already
+// known while step i's chain runs, and the chain adds the newest row; HS = 0
+// leaves the whole window to the chain warps.
+template <int SYS, int HS>
+__global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) adjoint_near_kernel(AdjArgs A, long long s, int nb) {
   using S = Sys<SYS>;
   constexpr int D = S::D, NP = S::NP, ld = kTrajPerTile * D;
+  constexpr int NT = 32 * (HS + 1) * D, HSX = HS > 0 ? HS : 1;
   extern __shared__ double adj_dyn[];
   double (*Wm)[ld] = reinterpret_cast<double (*)[ld]>(adj_dyn);            // mu~ rows s..s+64
   double (*Wl)[ld] = reinterpret_cast<double (*)[ld]>(adj_dyn + 65 * ld);  // lambda~ rows s..s+64
+  // helpers' partial window sums, [step parity][slice][column]
+  double (*Rm)[HSX][ld] = reinterpret_cast<double (*)[HSX][ld]>(adj_dyn + 130 * ld);
+  double (*Rl)[HSX][ld] = reinterpret_cast<double (*)[HSX][ld]>(adj_dyn + (130 + 2 * HS) * ld);
   __shared__ double wsb[65], wsa[65];
   __shared__ double xsh[D][32];
-  const int tile = blockIdx.x, c = threadIdx.x >> 5, lane = threadIdx.x & 31, col = lane * D + c;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool chain = warp < D;
+  const int c = chain ? warp : (warp - D) % D;  // component (column group)
+  const int q = chain ? 0 : (warp - D) / D;     // helper slice
+  const int tile = blockIdx.x, col = lane * D + c;
   const TileDesc& T = A.tiles[tile];
   const int traj = T.traj[lane];
   const int src = traj >= 0 ? traj : T.traj[0];
-  const double alpha = A.bucket_alpha[T.bucket];
   const double* wb = A.bucket_b[T.bucket];
   const double* wa = A.bucket_a[T.bucket];
-  const double* wc = A.bucket_c[T.bucket];
-  const double g = A.bucket_g[T.bucket];
-  const long long Ni = traj >= 0 ? (long long)A.N[traj] : -1;
-  const double h = A.h[src];
-  const double hh = traj >= 0 ? A.hhat[traj] : 0.0;
-  double p[kMaxParams];
-#pragma unroll
-  for (int q = 0; q < NP; ++q) p[q] = A.params[(size_t)src * NP + q];
   double* Xm = A.X + A.atiles[2 * tile].f_off;
   double* Xl = A.X + A.atiles[2 * tile + 1].f_off;
-  for (int m = threadIdx.x; m < 65; m += 32 * D) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
-  Wm[0][col] = Xm[s * ld + col];
-  Wl[0][col] = Xl[s * ld + col];
-  double adp[NP], ady0 = 0.0, phc = 0.0;
-#pragma unroll
-  for (int q = 0; q < NP; ++q) adp[q] = 0.0;
-  if (traj >= 0) {
-#pragma unroll
-    for (int q = 0; q < NP; ++q) adp[q] = A.acc_dp[((size_t)traj * D + c) * NP + q];
-    ady0 = A.acc_dy0[(size_t)traj * D + c];
-    phc = A.phi0c[(size_t)traj * D + c];
+  for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
+  for (int m = threadIdx.x; m < ld; m += NT) {
+    Wm[0][m] = Xm[s * ld + m];
+    Wl[0][m] = Xl[s * ld + m];
   }
-  __syncthreads();
-  const size_t fstride = (size_t)A.far_tiles * 2 * A.B * ld;
-  for (int i = 0; i < nb; ++i) {
-    const long long t = s + i;
-    const long long k = Ni - 1 - t;  // forward index of this reverse step
-    const bool act = k >= 0;
-    const long long kk = act ? k : 0;
-    // inputs at k: y_k, y^P_k, G_k
-    double yk[D], ypk[D];
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      yk[q] = A.Y[((size_t)src * A.ldY + kk) * D + q];
-      ypk[q] = A.YP[((size_t)src * A.ldY + kk) * D + q];
-    }
-    const double Gk = A.G[((size_t)src * A.ldY + kk) * D + c];
-    // far sums (mu~ rows through b, lambda~ rows through a)
-    double Sm = 0.0, Sl = 0.0;
-    if (s > 0) {
-      for (int q = 0; q < A.far_ksplit; ++q) {
-        Sm += A.far[q * fstride + ((((size_t)2 * tile) * 2 + 0) * A.B + i) * ld + col];
-        Sl += A.far[q * fstride + ((((size_t)2 * tile + 1) * 2 + 1) * A.B + i) * ld + col];
-      }
-    }
-    for (int r = 0; r <= i; ++r) {
-      Sm = fma(wsb[i - r], Wm[r][col], Sm);
-      Sl = fma(wsa[i - r], Wl[r][col], Sl);
-    }
-    const double phi = hh * (Sm + (k >= 1 ? Sl : phc));
-    xsh[c][lane] = phi;
-    bar_components<D>();
-    // Jacobians recomputed from the stored states: at y_k and at y^P_k
-    double Jy[D * D], Qy[D * NP], Jp[D * D], Qp[D * NP];
-    S::jac(p, alpha, (double)kk * h, yk, Jy, Qy);
-    S::jac(p, alpha, (double)kk * h, ypk, Jp, Qp);
-    double lam = Gk;
-#pragma unroll
-    for (int j = 0; j < D; ++j) lam = fma(Jy[j * D + c], xsh[j][lane], lam);
-    bar_components<D>();
-    xsh[c][lane] = lam;
-    bar_components<D>();
-    double jl = 0.0;
-#pragma unroll
-    for (int j = 0; j < D; ++j) jl = fma(Jp[j * D + c], xsh[j][lane], jl);
-    bar_components<D>();
-    const double mu = hh * g * jl;
-    if (act) {
-#pragma unroll
-      for (int q = 0; q < NP; ++q) adp[q] = fma(Qy[c * NP + q], phi, adp[q]);
-      if (k >= 1) {
-#pragma unroll
-        for (int q = 0; q < NP; ++q) adp[q] = fma(hh * g * Qp[c * NP + q], lam, adp[q]);
-        ady0 += lam + mu;
-        phc = fma(wc[k - 1], lam, phc);
-      } else {  // k = 0: lambda here is G_0 + J_0^T phi_0
-        A.dy0[(size_t)traj * D + c] = ady0 + lam;
-      }
-      if (!(isfinite(lam) && isfinite(phi))) report_status(A.status, ABM_ERR_NONFINITE, traj, k);
-    }
-    const bool row = act && k >= 1;
-    Wm[i + 1][col] = row ? mu : 0.0;
-    Wl[i + 1][col] = row ? lam : 0.0;
-    Xm[(t + 1) * ld + col] = row ? mu : 0.0;
-    Xl[(t + 1) * ld + col] = row ? lam : 0.0;
+  for (int m = threadIdx.x; m < HS * ld; m += NT) {  // step 0 has no earlier window rows
+    Rm[0][m / ld][m % ld] = 0.0;
+    Rl[0][m / ld][m % ld] = 0.0;
   }
-  if (traj >= 0) {
+
+  if (chain) {
+    const double alpha = A.bucket_alpha[T.bucket];
+    const double* wc = A.bucket_c[T.bucket];
+    const double g = A.bucket_g[T.bucket];
+    const long long Ni = traj >= 0 ? (long long)A.N[traj] : -1;
+    const double h = A.h[src];
+    const double hh = traj >= 0 ? A.hhat[traj] : 0.0;
+    double p[kMaxParams];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) A.acc_dp[((size_t)traj * D + c) * NP + q] = adp[q];
-    A.acc_dy0[(size_t)traj * D + c] = ady0;
-    A.phi0c[(size_t)traj * D + c] = phc;
+    for (int k = 0; k < NP; ++k) p[k] = A.params[(size_t)src * NP + k];
+    double adp[NP], ady0 = 0.0, phc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) adp[k] = 0.0;
+    if (traj >= 0) {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) adp[k] = A.acc_dp[((size_t)traj * D + c) * NP + k];
+      ady0 = A.acc_dy0[(size_t)traj * D + c];
+      phc = A.phi0c[(size_t)traj * D + c];
+    }
+    __syncthreads();
+    const size_t fstride = (size_t)A.far_tiles * 2 * A.B * ld;
+    for (int i = 0; i < nb; ++i) {
+      const long long t = s + i;
+      const long long k = Ni - 1 - t;  // forward index of this reverse step
+      const bool act = k >= 0;
+      const long long kk = act ? k : 0;
+      const int par = i & 1;
+      // inputs at k: y_k, y^P_k, G_k
+      double yk[D], ypk[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        yk[j] = A.Y[((size_t)src * A.ldY + kk) * D + j];
+        ypk[j] = A.YP[((size_t)src * A.ldY + kk) * D + j];
+      }
+      const double Gk = A.G[((size_t)src * A.ldY + kk) * D + c];
+      // far sums (mu~ rows through b, lambda~ rows through a)
+      double Sm = 0.0, Sl = 0.0;
+      if (s > 0) {
+        for (int kq = 0; kq < A.far_ksplit; ++kq) {
+          Sm += A.far[kq * fstride + ((((size_t)2 * tile) * 2 + 0) * A.B + i) * ld + col];
+          Sl += A.far[kq * fstride + ((((size_t)2 * tile + 1) * 2 + 1) * A.B + i) * ld + col];
+        }
+      }
+      if constexpr (HS > 0) {
+#pragma unroll
+        for (int j = 0; j < HS; ++j) { Sm += Rm[par][j][col]; Sl += Rl[par][j][col]; }
+        Sm = fma(wsb[0], Wm[i][col], Sm);  // the newest window row
+        Sl = fma(wsa[0], Wl[i][col], Sl);
+      } else {  // the whole window, rows [0, i], two chains per sum
+        double Sm1 = 0.0, Sl1 = 0.0;
+        int r = 0;
+        for (; r + 1 <= i; r += 2) {
+          Sm = fma(wsb[i - r], Wm[r][col], Sm);
+          Sl = fma(wsa[i - r], Wl[r][col], Sl);
+          Sm1 = fma(wsb[i - r - 1], Wm[r + 1][col], Sm1);
+          Sl1 = fma(wsa[i - r - 1], Wl[r + 1][col], Sl1);
+        }
+        if (r <= i) {
+          Sm = fma(wsb[i - r], Wm[r][col], Sm);
+          Sl = fma(wsa[i - r], Wl[r][col], Sl);
+        }
+        Sm += Sm1;
+        Sl += Sl1;
+      }
+      const double phi = hh * (Sm + (k >= 1 ? Sl : phc));
+      xsh[c][lane] = phi;
+      bar_components<D>();
+      // Jacobians recomputed from the stored states: at y_k and at y^P_k; this
+      // warp uses column c of J and row c of Q (selected with compile-time
+      // indices so that the arrays stay in registers)
+      double Jy[D * D], Qy[D * NP], Jp[D * D], Qp[D * NP];
+      S::jac(p, alpha, (double)kk * h, yk, Jy, Qy);
+      S::jac(p, alpha, (double)kk * h, ypk, Jp, Qp);
+      double Jyc[D], Jpc[D], Qyc[NP], Qpc[NP];
+#pragma unroll
+      for (int j = 0; j < D; ++j) { Jyc[j] = Jy[j * D]; Jpc[j] = Jp[j * D]; }
+#pragma unroll
+      for (int j = 0; j < NP; ++j) { Qyc[j] = Qy[j]; Qpc[j] = Qp[j]; }
+#pragma unroll
+      for (int cc = 1; cc < D; ++cc) {
+        if (c == cc) {
+#pragma unroll
+          for (int j = 0; j < D; ++j) { Jyc[j] = Jy[j * D + cc]; Jpc[j] = Jp[j * D + cc]; }
+#pragma unroll
+          for (int j = 0; j < NP; ++j) { Qyc[j] = Qy[cc * NP + j]; Qpc[j] = Qp[cc * NP + j]; }
+        }
+      }
+      double lam = Gk;
+#pragma unroll
+      for (int j = 0; j < D; ++j) lam = fma(Jyc[j], xsh[j][lane], lam);
+      bar_components<D>();
+      xsh[c][lane] = lam;
+      bar_components<D>();
+      double jl = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) jl = fma(Jpc[j], xsh[j][lane], jl);
+      bar_components<D>();
+      const double mu = hh * g * jl;
+      if (act) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) adp[j] = fma(Qyc[j], phi, adp[j]);
+        if (k >= 1) {
+#pragma unroll
+          for (int j = 0; j < NP; ++j) adp[j] = fma(hh * g * Qpc[j], lam, adp[j]);
+          ady0 += lam + mu;
+          phc = fma(wc[k - 1], lam, phc);
+        } else {  // k = 0: lambda here is G_0 + J_0^T phi_0
+          A.dy0[(size_t)traj * D + c] = ady0 + lam;
+        }
+        if (!(isfinite(lam) && isfinite(phi))) report_status(A.status, ABM_ERR_NONFINITE, traj, k);
+      }
+      const bool row = act && k >= 1;
+      Wm[i + 1][col] = row ? mu : 0.0;
+      Wl[i + 1][col] = row ? lam : 0.0;
+      Xm[(t + 1) * ld + col] = row ? mu : 0.0;
+      Xl[(t + 1) * ld + col] = row ? lam : 0.0;
+      __syncthreads();
+    }
+    if (traj >= 0) {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) A.acc_dp[((size_t)traj * D + c) * NP + j] = adp[j];
+      A.acc_dy0[(size_t)traj * D + c] = ady0;
+      A.phi0c[(size_t)traj * D + c] = phc;
+    }
+  } else {
+    __syncthreads();
+    for (int i = 0; i < nb; ++i) {
+      if (i + 1 < nb) {
+        // partial window sums of step i+1 over rows r in [0, i], r = q mod HS
+        const int nxt = (i + 1) & 1;
+        double sm0 = 0.0, sl0 = 0.0, sm1 = 0.0, sl1 = 0.0;
+        int r = q;
+#pragma unroll 1
+        for (; r + HSX <= i; r += 2 * HSX) {
+          sm0 = fma(wsb[i + 1 - r], Wm[r][col], sm0);
+          sl0 = fma(wsa[i + 1 - r], Wl[r][col], sl0);
+          sm1 = fma(wsb[i + 1 - r - HSX], Wm[r + HSX][col], sm1);
+          sl1 = fma(wsa[i + 1 - r - HSX], Wl[r + HSX][col], sl1);
+        }
+        if (r <= i) {
+          sm0 = fma(wsb[i + 1 - r], Wm[r][col], sm0);
+          sl0 = fma(wsa[i + 1 - r], Wl[r][col], sl0);
+        }
+        Rm[nxt][q][col] = sm0 + sm1;
+        Rl[nxt][q][col] = sl0 + sl1;
+      }
+      __syncthreads();
+    }
   }
   if (A.Xsh) {
     __syncthreads();
-    // BF16 split rows s..s+63 of both histories, K-major 16-byte stores
+    // BF16 split rows s..s+63 of both histories: K block s / 64 of adjoint
+    // tiles 2 tile + hist (K-block tiled like the forward history pieces)
     constexpr int UNITS = 2 * 3 * ld * 8;
-    for (int u = threadIdx.x; u < UNITS; u += 32 * D) {
+    for (int u = threadIdx.x; u < UNITS; u += NT) {
       const int hist = u / (3 * ld * 8), rem0 = u % (3 * ld * 8);
       const int pc = rem0 / (ld * 8), rem = rem0 % (ld * 8);
       const int cc = rem / 8, part = rem % 8;
@@ -213,7 +293,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_near_kernel(AdjArgs 
         v[r] = pcs[pc];
       }
       __nv_bfloat16* dst = A.Xsh + (size_t)pc * A.xsh_plane +
-                           ((size_t)(2 * tile + hist) * ld + cc) * A.xsh_ld + s + part * 8;
+                           (((size_t)(2 * tile + hist) * (A.xsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
       *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
     }
   }
@@ -237,24 +317,32 @@ cudaError_t launch_adjoint_setup(int sys, const AdjArgs& A, int n_tiles, cudaStr
   return cudaGetLastError();
 }
 
-template <int SYS>
+template <int SYS, int HS>
 cudaError_t launch_adjoint_near_t(const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
   constexpr int D = Sys<SYS>::D;
-  const size_t smem = (size_t)2 * 65 * kTrajPerTile * D * sizeof(double);
-  static bool attr_set = false;
+  const size_t smem = (size_t)(130 + 4 * HS) * kTrajPerTile * D * sizeof(double);
+  static bool attr_set = false;  // per instantiation
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(adjoint_near_kernel<SYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(adjoint_near_kernel<SYS, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  adjoint_near_kernel<SYS><<<n_active, 32 * D, smem, st>>>(A, s, nb);
+  adjoint_near_kernel<SYS, HS><<<n_active, 32 * (HS + 1) * D, smem, st>>>(A, s, nb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+// wpc: warps per state component, 1 (chain only), 2 or 3 (chain + helpers)
+cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, int wpc,
+                                cudaStream_t st) {
   cudaError_t err = cudaErrorInvalidValue;
-  ABM_DISPATCH_SYSTEM(sys, err = (launch_adjoint_near_t<SYS>(A, n_active, s, nb, st)));
+  if (wpc == 3) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_adjoint_near_t<SYS, 2>(A, n_active, s, nb, st)));
+  } else if (wpc == 2) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_adjoint_near_t<SYS, 1>(A, n_active, s, nb, st)));
+  } else if (wpc == 1) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_adjoint_near_t<SYS, 0>(A, n_active, s, nb, st)));
+  }
   return err;
 }
 

@@ -31,11 +31,11 @@ cudaError_t launch_build_wx(const double* b, const double* a, long long Mw, long
                             __nv_bfloat16* Wx, cudaStream_t st);
 bool make_tmap_bf16(CUtensorMap* out, void* base, unsigned long long inner, unsigned long long rows,
                     unsigned box_rows);
-cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long ld, long long plane,
-                            cudaStream_t st);
+cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long plane, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* far, int ksplit, int n_tiles, double* P, double* C, cudaStream_t st);
 cudaError_t launch_adjoint_setup(int sys, const AdjArgs& A, int n_tiles, cudaStream_t st);
-cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st);
+cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, int wpc,
+                                cudaStream_t st);
 cudaError_t launch_adjoint_finish(int sys, const AdjArgs& A, int M, cudaStream_t st);
 }  // namespace abm
 
@@ -215,6 +215,29 @@ abm_status get_weights(abm_plan p, double alpha, cudaStream_t st, WeightSet** ou
 }
 
 
+// History split of the tensor-core far kernel (CTAs per column tile).  The
+// kernel runs one CTA per SM, so n_tiles * ks CTAs take ceil(n_tiles * ks /
+// sms) waves, each as long as one CTA: a fixed part (TMEM and barrier setup,
+// pipeline fill, the FP64 reductions at the end; about kFarCtaSetupBlocks
+// K blocks of streaming) plus its ceil(nkb / ks) K blocks.  Picks the split
+// with the least modelled time among those within max_waves waves, so a
+// split never spills a few CTAs into an extra, mostly idle wave.
+constexpr double kFarCtaSetupBlocks = 6.0;
+int far_ksplit(int n_tiles, int nkb, int sms, int max_waves) {
+  int best = 1;
+  double best_cost = 1e300;
+  for (int ks = 1; ks <= nkb; ++ks) {
+    const long long waves = ((long long)n_tiles * ks + sms - 1) / sms;
+    if (ks > 1 && waves > max_waves) break;
+    const double cost = (double)waves * (kFarCtaSetupBlocks + (double)((nkb + ks - 1) / ks));
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = ks;
+    }
+  }
+  return best;
+}
+
 // abm_far_history on a tensor-core plan: one column tile of 96 columns, history
 // rows [1, s) with s a multiple of 64 (the tensor path always covers whole
 // 64-row blocks from row 0, whose BF16 copy is zero).
@@ -228,10 +251,10 @@ abm_status far_history_tc(abm_plan p, double alpha, const double* F, long long r
   abm_status rs = get_weights(p, alpha, st, &w);
   if (rs) return rs;
   const long long gcols = (long long)p->max_tiles * kTrajPerTile * p->d;
-  CK(launch_fill_fsh(F, s, p->Fsh, p->fsh_ld, gcols * p->fsh_ld, st), "fill history pieces");
+  CK(launch_fill_fsh(F, s, p->Fsh, gcols * p->fsh_ld, st), "fill history pieces");
   CUtensorMap mw[3];
   for (int q = 0; q < 3; ++q)
-    if (!make_tmap_bf16(&mw[q], w->Wx + (size_t)q * 128 * p->Lx, (unsigned long long)p->Lx, 128, 128))
+    if (!make_tmap_bf16(&mw[q], w->Wx + (size_t)q * 128 * p->Lx, 64, (unsigned long long)(2 * p->Lx), 128))
       return fail(p, ABM_ERR_CUDA, "abm_far_history: tensor map");
   CK(cudaMemcpyAsync(p->d_tmapW, mw, sizeof(mw), cudaMemcpyHostToDevice, st), "tmaps");
   TileDesc td{};
@@ -240,10 +263,11 @@ abm_status far_history_tc(abm_plan p, double alpha, const double* F, long long r
   td.n_tile = (int)s + 64;
   CK(cudaMemcpyAsync(p->d_tiles, &td, sizeof(td), cudaMemcpyHostToDevice, st), "tile");
   const int nkb_total = (int)(s / 64);
-  const int ks = std::max(1, std::min(nkb_total, 2 * p->sms));
+  const int ks = far_ksplit(1, nkb_total, p->sms, 2);
   CK(cudaMemsetAsync(p->farb, 0, (size_t)2 * 64 * 96 * sizeof(double), st), "far sums reset");
   FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
-              p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, 1, ks};
+              p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, 1, ks,
+              (int)(p->fsh_ld / 64)};
   CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, 1, st), "tensor-core far kernel");
   CK(launch_sum_partials(p->farb, ks, 1, P, C, st), "partial sums");
   CK(cudaStreamSynchronize(st), "synchronize");  // the host-staged tile descriptor must outlive the copy
@@ -340,8 +364,8 @@ abm_status schedule_batch(abm_plan p, int M, const double* alpha, const double* 
     std::vector<CUtensorMap> mw(ualpha.size() * 3);
     for (size_t g = 0; g < ualpha.size(); ++g)
       for (int q = 0; q < 3; ++q)
-        if (!make_tmap_bf16(&mw[g * 3 + q], ws[g]->Wx + (size_t)q * 128 * p->Lx, (unsigned long long)p->Lx, 128,
-                            128))
+        if (!make_tmap_bf16(&mw[g * 3 + q], ws[g]->Wx + (size_t)q * 128 * p->Lx, 64,
+                            (unsigned long long)(2 * p->Lx), 128))
           return fail(p, ABM_ERR_CUDA, std::string(who) + ": tensor map of the Toeplitz pieces");
     CK(cudaMemcpyAsync(p->d_tmapW, mw.data(), mw.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st), "tmaps");
   }
@@ -366,12 +390,14 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
       if (tc_prec) {
         const int nkb_total = (int)(s / 64);
         const int waves = p->o.far_split > 0 ? p->o.far_split : 2;
-        const int ks = std::max(1, std::min(nkb_total, (waves * p->sms + n_active - 1) / n_active));
+        const int ks = far_ksplit(n_active, nkb_total, p->sms, waves);
         A.ksplit = 1;  // the K-split parts are added on the device
-        CK(cudaMemsetAsync(p->farb, 0, (size_t)n_active * 2 * B * kTrajPerTile * d * sizeof(double), st),
-           "far sums reset");
+        if (ks > 1)  // split tiles add their parts; unsplit tiles store
+          CK(cudaMemsetAsync(p->farb, 0, (size_t)n_active * 2 * B * kTrajPerTile * d * sizeof(double), st),
+             "far sums reset");
         FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
-                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, n_active, ks};
+                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, n_active, ks,
+                    (int)(p->fsh_ld / 64)};
         Trace tr(p, ABM_KERNEL_FAR, st);
         CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, n_active, st), "tensor-core far kernel");
       } else {
@@ -381,10 +407,12 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
     }
     {
       Trace tr(p, ABM_KERNEL_NEAR, st);
-      // warps per component: latency when few tiles are active, throughput when many
-      const int qw = p->o.near_warps ? p->o.near_warps
-                                     : (n_active <= p->sms ? 4 : (n_active <= 2 * p->sms ? 2 : 1));
-      CK(launch_batched_near(p->sys, A, n_active, s, B, qw, st), "near kernel");
+      // warps per component: helpers hide the chain's latency when few tiles are
+      // active; with many tiles per SM the tiles hide each other's and the
+      // chain-only form needs fewer instructions
+      const int wpc = p->o.near_warps ? p->o.near_warps
+                                      : (n_active <= p->sms ? 3 : (n_active <= 2 * p->sms ? 2 : 1));
+      CK(launch_batched_near(p->sys, A, n_active, s, B, wpc, st), "near kernel");
     }
   }
   return ABM_OK;
@@ -421,7 +449,7 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
   for (int r : o->reserved)
     if (r) return ABM_ERR_INVALID_ARG;
   if (o->tile_B && o->tile_B != 64 && o->tile_B != 32) return ABM_ERR_UNSUPPORTED;
-  if (o->near_warps != 0 && o->near_warps != 1 && o->near_warps != 2 && o->near_warps != 4)
+  if (o->near_warps != 0 && o->near_warps != 1 && o->near_warps != 2 && o->near_warps != 3 && o->near_warps != 5)
     return ABM_ERR_INVALID_ARG;
   if (o->far_split < 0 || o->far_split > 64) return ABM_ERR_INVALID_ARG;
   const bool tc_prec = o->prec == ABM_PREC_BF16X3_FAR || o->prec == ABM_PREC_BF16X6_FAR;
@@ -494,7 +522,7 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
         return cleanup_fail(ABM_ERR_OOM);
       CUtensorMap mf[3];
       for (int q = 0; q < 3; ++q)
-        if (!make_tmap_bf16(&mf[q], p->Fsh + (size_t)q * gcols * p->fsh_ld, (unsigned long long)p->fsh_ld, gcols,
+        if (!make_tmap_bf16(&mf[q], p->Fsh + (size_t)q * gcols * p->fsh_ld, 64, gcols * (p->fsh_ld / 64),
                             (unsigned)(kTrajPerTile * d)))
           return cleanup_fail(ABM_ERR_CUDA);
       if (cudaMemcpy(p->d_tmapF, mf, sizeof(mf), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -778,7 +806,7 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
       CK(cudaMalloc(&p->d_tmapX, 3 * sizeof(CUtensorMap)), "adjoint tensor maps");
       CUtensorMap mx[3];
       for (int q = 0; q < 3; ++q)
-        if (!make_tmap_bf16(&mx[q], p->Xsh + (size_t)q * gcols * p->fsh_ld, (unsigned long long)p->fsh_ld, gcols,
+        if (!make_tmap_bf16(&mx[q], p->Xsh + (size_t)q * gcols * p->fsh_ld, 64, gcols * (p->fsh_ld / 64),
                             (unsigned)(kTrajPerTile * d)))
           return fail(p, ABM_ERR_CUDA, "abm_adjoint: tensor map of the adjoint planes");
       CK(cudaMemcpy(p->d_tmapX, mx, sizeof(mx), cudaMemcpyHostToDevice), "adjoint tensor maps");
@@ -854,10 +882,13 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
     if (s > 0) {
       if (tc_prec) {
         const int nkb_total = (int)(s / 64);
-        const int ks = std::max(1, std::min(nkb_total, (2 * p->sms + na2 - 1) / na2));
-        CK(cudaMemsetAsync(p->farb, 0, (size_t)na2 * 2 * B * kTrajPerTile * d * sizeof(double), st), "far sums reset");
+        const int ks = far_ksplit(na2, nkb_total, p->sms, p->o.far_split > 0 ? p->o.far_split : 2);
+        if (ks > 1)
+          CK(cudaMemsetAsync(p->farb, 0, (size_t)na2 * 2 * B * kTrajPerTile * d * sizeof(double), st),
+             "far sums reset");
         FarTcArgs T{p->d_atiles, p->d_tmapW, p->d_tmapX, p->farb, p->status, s, p->Lbase,
-                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, na2, ks};
+                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, na2, ks,
+                    (int)(p->fsh_ld / 64)};
         Trace tr(p, ABM_KERNEL_ADJOINT, st);
         CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, na2, st), "adjoint tensor-core far kernel");
       } else {
@@ -871,7 +902,10 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
       }
     }
     Trace tr(p, ABM_KERNEL_ADJOINT, st);
-    CK(launch_adjoint_near(p->sys, A, n_active, s, B, st), "adjoint near kernel");
+    // warps per component as in the forward near kernel (5 is not built here)
+    const int wpc = p->o.near_warps ? std::min(p->o.near_warps, 3)
+                                    : (n_active <= p->sms ? 3 : (n_active <= 2 * p->sms ? 2 : 1));
+    CK(launch_adjoint_near(p->sys, A, n_active, s, B, wpc, st), "adjoint near kernel");
   }
   {
     Trace tr(p, ABM_KERNEL_ADJOINT, st);

@@ -56,12 +56,20 @@ __global__ void batched_setup_kernel(BatchArgs A) {
 
 // ---------------------------------------------------------------------------
 // Near kernel: one CTA per column tile, nb sequential PECE steps in FP64, one
-// lane per trajectory.  QW warps per state component each sum one slice of
-// the window lags (rows k with k - e = q mod QW) out of a shared-memory copy
-// of the tile's f rows; warp q = 0 of component c adds the slices and runs the
-// chain for that component (y^P, f(y^P), y, f(y)); the components meet
-// through shared memory before each evaluation of f.  QW trades FP64 latency
-// per step (few tiles) against throughput (many tiles per SM).
+// lane per trajectory.  The window sums of step i+1 over rows already known
+// (all but the newest, f_{s+i+1}) do not depend on step i, so they run one
+// step ahead of the chain:
+//   chain warps  (D, warp c = component c): add the far sums, the j = 0
+//     terms, the helpers' partial window sums and the newest row term, then
+//     y^P, f(y^P), y, f(y); the components meet through shared memory before
+//     each evaluation of f (named barrier 1)
+//   helper warps (HS per component): while step i's chain runs, helper
+//     (c, q) sums rows r = q mod HS of step i+1's window over rows already in
+//     shared memory, into a double-buffered partial-sum slot
+// so the window (the FP64-throughput part) overlaps the chain (the FP64-
+// latency part) instead of following it.  One barrier per step.  HS = 0: no
+// helpers, each chain warp sums its whole window itself (fewer instructions;
+// best when several tiles share an SM and hide each other's latency).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void split3_bf16(double x, __nv_bfloat16* out) {
   out[0] = __double2bfloat16(x);
@@ -71,23 +79,26 @@ __device__ __forceinline__ void split3_bf16(double x, __nv_bfloat16* out) {
   out[2] = __double2bfloat16(r);
 }
 
-template <int SYS, int QW>
-__global__ void __launch_bounds__(32 * QW * Sys<SYS>::D) batched_near_kernel(BatchArgs A, long long s, int nb) {
+template <int SYS, int HS>
+__global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kernel(BatchArgs A, long long s, int nb) {
   using S = Sys<SYS>;
   constexpr int D = S::D;
-  constexpr int NT = 32 * QW * D;
+  constexpr int NT = 32 * (HS + 1) * D;
   constexpr int ld = kTrajPerTile * D;  // columns of the tile history
   // dynamic shared memory: f rows s..s+64 of this tile (FP64, the window every
-  // sum reads) and the window partial sums of each lag slice
+  // sum reads) and the helpers' partial sums, [step parity][slice][column]
   extern __shared__ double near_dyn[];
   double (*Fw)[ld] = reinterpret_cast<double (*)[ld]>(near_dyn);
-  double (*Rp)[ld] = reinterpret_cast<double (*)[ld]>(near_dyn + 65 * ld);
-  double (*Rc)[ld] = reinterpret_cast<double (*)[ld]>(near_dyn + (65 + QW) * ld);
+  constexpr int HSX = HS > 0 ? HS : 1;
+  double (*Rp)[HSX][ld] = reinterpret_cast<double (*)[HSX][ld]>(near_dyn + 65 * ld);
+  double (*Rc)[HSX][ld] = reinterpret_cast<double (*)[HSX][ld]>(near_dyn + (65 + 2 * HS) * ld);
   __shared__ double ysh[2][D][32], ysh2[2][D][32];  // predictor / corrector exchange
   __shared__ double wsb[65], wsa[65];               // lags 0..64 of this tile's weights
   __shared__ double bns[64], cns[64];               // b_n, c_n of this tile's targets
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = warp % D, q = warp / D;  // component, lag slice
+  const bool chain = warp < D;
+  const int c = chain ? warp : (warp - D) % D;  // component (column group)
+  const int q = chain ? 0 : (warp - D) / D;     // helper slice
   const int tile = blockIdx.x;
   const TileDesc& T = A.tiles[tile];
   const int traj = T.traj[lane];
@@ -96,44 +107,45 @@ __global__ void __launch_bounds__(32 * QW * Sys<SYS>::D) batched_near_kernel(Bat
   const double* __restrict__ wb = A.bucket_b[T.bucket];
   const double* __restrict__ wa = A.bucket_a[T.bucket];
   const double* __restrict__ wc = A.bucket_c[T.bucket];
-  const double g = A.bucket_g[T.bucket];
-  const long long Ntraj = traj >= 0 ? (long long)A.N[traj] : 0;
-  const double h = A.h[src];
-  const double hh = traj >= 0 ? A.hhat[traj] : pow(h, alpha);
-  double p[kMaxParams];
-#pragma unroll
-  for (int k = 0; k < S::NP; ++k) p[k] = A.params[(size_t)src * S::NP + k];
-  const double y0c = A.y0[(size_t)src * D + c];
-  double* __restrict__ F = A.F + T.f_off;
-  float* __restrict__ F32 = A.F32 ? A.F32 + T.f_off : nullptr;
   const int col = lane * D + c;  // this thread's history column
-  const double F0c = F[col];
-  if (q == 0) Fw[0][col] = F[s * ld + col];
+  double* __restrict__ F = A.F + T.f_off;
   for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
   for (int m = threadIdx.x; m < 64; m += NT) { bns[m] = wb[s + m]; cns[m] = wc[s + m]; }
-  const int kfirst = s > 1 ? 0 : 1;  // window rows relative to s (row 0 is f_0 when s = 0)
-  const double* __restrict__ farP = A.far + (((size_t)tile * 2) * A.B) * ld + col;
-  const size_t far_q_stride = (size_t)A.n_tiles * 2 * A.B * ld;
-  const size_t far_c_off = (size_t)A.B * ld;
-  // far partial sums + k = 0 terms of the next target, loaded a step ahead
-  double nxp = 0.0, nxc = 0.0;
-  if (q == 0 && s > 1) {
-    for (int kq = 0; kq < A.ksplit; ++kq) {
-      nxp += farP[kq * far_q_stride];
-      nxc += farP[kq * far_q_stride + far_c_off];
-    }
+  for (int m = threadIdx.x; m < ld; m += NT) Fw[0][m] = F[s * ld + m];
+  for (int m = threadIdx.x; m < HS * ld; m += NT) {  // step 0 has no earlier window rows (helpers)
+    Rp[0][m / ld][m % ld] = 0.0;
+    Rc[0][m / ld][m % ld] = 0.0;
   }
-  bool reported = false;
-  __syncthreads();
-  for (int i = 0; i < nb; ++i) {
-    const long long n = s + i;
-    const int par = i & 1;
-    // slice q of the window sums over rows r in [kfirst, i] (r = q mod QW);
-    // two accumulator chains per sum
-    double sp0 = 0.0, sc0 = 0.0, sp1 = 0.0, sc1 = 0.0;
-    if (q == 0) {
-      sp0 = fma(bns[i], F0c, nxp);
-      sc0 = fma(cns[i], F0c, nxc);
+  const int kfirst = s > 1 ? 0 : 1;  // window rows relative to s (row 0 is f_0 when s = 0)
+
+  if (chain) {
+    const double g = A.bucket_g[T.bucket];
+    const long long Ntraj = traj >= 0 ? (long long)A.N[traj] : 0;
+    const double h = A.h[src];
+    const double hh = traj >= 0 ? A.hhat[traj] : pow(h, alpha);
+    double p[kMaxParams];
+#pragma unroll
+    for (int k = 0; k < S::NP; ++k) p[k] = A.params[(size_t)src * S::NP + k];
+    const double y0c = A.y0[(size_t)src * D + c];
+    float* __restrict__ F32 = A.F32 ? A.F32 + T.f_off : nullptr;
+    const double F0c = F[col];
+    const double* __restrict__ farP = A.far + (((size_t)tile * 2) * A.B) * ld + col;
+    const size_t far_q_stride = (size_t)A.n_tiles * 2 * A.B * ld;
+    const size_t far_c_off = (size_t)A.B * ld;
+    // far partial sums of the next target, loaded a step ahead
+    double nxp = 0.0, nxc = 0.0;
+    if (s > 1) {
+      for (int kq = 0; kq < A.ksplit; ++kq) {
+        nxp += farP[kq * far_q_stride];
+        nxc += farP[kq * far_q_stride + far_c_off];
+      }
+    }
+    bool reported = false;
+    __syncthreads();
+    for (int i = 0; i < nb; ++i) {
+      const long long n = s + i;
+      const int par = i & 1;
+      double sp = fma(bns[i], F0c, nxp), sc = fma(cns[i], F0c, nxc);
       nxp = nxc = 0.0;
       if (s > 1 && i + 1 < nb) {
         for (int kq = 0; kq < A.ksplit; ++kq) {
@@ -141,30 +153,31 @@ __global__ void __launch_bounds__(32 * QW * Sys<SYS>::D) batched_near_kernel(Bat
           nxc += farP[kq * far_q_stride + far_c_off + (size_t)(i + 1) * ld];
         }
       }
-    }
-    int r = kfirst + ((q - kfirst) % QW + QW) % QW;
-    for (; r + QW <= i; r += 2 * QW) {
-      const double f0 = Fw[r][col], f1 = Fw[r + QW][col];
-      sp0 = fma(wsb[i - r], f0, sp0);
-      sc0 = fma(wsa[i - r], f0, sc0);
-      sp1 = fma(wsb[i - r - QW], f1, sp1);
-      sc1 = fma(wsa[i - r - QW], f1, sc1);
-    }
-    if (r <= i) {
-      const double f0 = Fw[r][col];
-      sp0 = fma(wsb[i - r], f0, sp0);
-      sc0 = fma(wsa[i - r], f0, sc0);
-    }
-    double sp = sp0 + sp1, sc = sc0 + sc1;
-    if (QW > 1) {
-      Rp[q][col] = sp;
-      Rc[q][col] = sc;
-      __syncthreads();
-    }
-    if (q == 0) {  // the chain: component c
-      if (QW > 1) {
+      if constexpr (HS > 0) {
 #pragma unroll
-        for (int k = 1; k < QW; ++k) { sp += Rp[k][col]; sc += Rc[k][col]; }
+        for (int k = 0; k < HS; ++k) { sp += Rp[par][k][col]; sc += Rc[par][k][col]; }
+        if (i >= kfirst) {  // the newest window row, f_{s+i}
+          const double fi = Fw[i][col];
+          sp = fma(wsb[0], fi, sp);
+          sc = fma(wsa[0], fi, sc);
+        }
+      } else {  // the whole window, rows [kfirst, i], two chains per sum
+        double sp1 = 0.0, sc1 = 0.0;
+        int r = kfirst;
+        for (; r + 1 <= i; r += 2) {
+          const double f0 = Fw[r][col], f1 = Fw[r + 1][col];
+          sp = fma(wsb[i - r], f0, sp);
+          sc = fma(wsa[i - r], f0, sc);
+          sp1 = fma(wsb[i - r - 1], f1, sp1);
+          sc1 = fma(wsa[i - r - 1], f1, sc1);
+        }
+        if (r <= i) {
+          const double f0 = Fw[r][col];
+          sp = fma(wsb[i - r], f0, sp);
+          sc = fma(wsa[i - r], f0, sc);
+        }
+        sp += sp1;
+        sc += sc1;
       }
       const double t1 = (double)(n + 1) * h;
       const double yp = fma(hh, sp, y0c);
@@ -192,14 +205,41 @@ __global__ void __launch_bounds__(32 * QW * Sys<SYS>::D) batched_near_kernel(Bat
           reported = true;
         }
       }
+      __syncthreads();
     }
-    if (QW > 1) __syncthreads();
-    else asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
+  } else {
+    __syncthreads();
+    for (int i = 0; i < nb; ++i) {
+      if (i + 1 < nb) {
+        // partial window sums of step i+1 over rows r in [kfirst, i], r = q mod HS
+        // (weights of lag i+1-r); two accumulator chains per sum
+        const int nxt = (i + 1) & 1;
+        double sp0 = 0.0, sc0 = 0.0, sp1 = 0.0, sc1 = 0.0;
+        int r = kfirst + ((q - kfirst) % HS + HS) % HS;
+#pragma unroll 1
+        for (; r + HS <= i; r += 2 * HS) {
+          const double f0 = Fw[r][col], f1 = Fw[r + HS][col];
+          sp0 = fma(wsb[i + 1 - r], f0, sp0);
+          sc0 = fma(wsa[i + 1 - r], f0, sc0);
+          sp1 = fma(wsb[i + 1 - r - HS], f1, sp1);
+          sc1 = fma(wsa[i + 1 - r - HS], f1, sc1);
+        }
+        if (r <= i) {
+          const double f0 = Fw[r][col];
+          sp0 = fma(wsb[i + 1 - r], f0, sp0);
+          sc0 = fma(wsa[i + 1 - r], f0, sc0);
+        }
+        Rp[nxt][q][col] = sp0 + sp1;
+        Rc[nxt][q][col] = sc0 + sc1;
+      }
+      __syncthreads();
+    }
   }
   __syncthreads();
   if (A.Fsh) {
-    // BF16 split of rows s..s+63, K-major: 8 rows of one column and piece per
-    // 16-byte store (row s of the first tile stays zero: the j = 0 term is FP64)
+    // BF16 split of rows s..s+63 = K block s / 64 of this column tile (K-block
+    // tiled, K-major inside): 8 rows of one column and piece per 16-byte store
+    // (row s of the first tile stays zero: the j = 0 term is FP64)
     constexpr int UNITS = 3 * ld * 8;
     for (int u = threadIdx.x; u < UNITS; u += NT) {
       const int pc = u / (ld * 8), rem = u % (ld * 8);
@@ -213,7 +253,7 @@ __global__ void __launch_bounds__(32 * QW * Sys<SYS>::D) batched_near_kernel(Bat
         v[r] = pcs[pc];
       }
       __nv_bfloat16* dst = A.Fsh + (size_t)pc * A.fsh_plane +
-                           ((size_t)blockIdx.x * ld + cc) * A.fsh_ld + s + part * 8;
+                           (((size_t)blockIdx.x * (A.fsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
       *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
     }
   }
@@ -341,30 +381,33 @@ cudaError_t launch_batched_setup(int sys, const BatchArgs& A, int n_tiles, cudaS
   return cudaGetLastError();
 }
 
-template <int SYS, int QW>
+template <int SYS, int HS>
 cudaError_t launch_near_t(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
   constexpr int D = Sys<SYS>::D;
-  const size_t smem = (size_t)(65 + 2 * QW) * kTrajPerTile * D * sizeof(double);
+  const size_t smem = (size_t)(65 + 4 * HS) * kTrajPerTile * D * sizeof(double);
   static bool attr_set = false;  // per instantiation; a plan is used from one thread
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(batched_near_kernel<SYS, QW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(batched_near_kernel<SYS, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  batched_near_kernel<SYS, QW><<<n_active, 32 * QW * D, smem, st>>>(A, s, nb);
+  batched_near_kernel<SYS, HS><<<n_active, 32 * (HS + 1) * D, smem, st>>>(A, s, nb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb, int qw,
+// wpc: warps per state component, 1 (chain only), 2, 3 or 5 (chain + helpers)
+cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb, int wpc,
                                 cudaStream_t st) {
   cudaError_t err = cudaErrorInvalidValue;
-  if (qw == 4) {
+  if (wpc == 5) {
     ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 4>(A, n_active, s, nb, st)));
-  } else if (qw == 2) {
+  } else if (wpc == 3) {
     ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 2>(A, n_active, s, nb, st)));
-  } else {
+  } else if (wpc == 2) {
     ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 1>(A, n_active, s, nb, st)));
+  } else if (wpc == 1) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 0>(A, n_active, s, nb, st)));
   }
   return err;
 }

@@ -40,8 +40,10 @@ struct BatchArgs {
   // histories
   double* F;               // FP64, per tile [rows][32*D]
   float* F32;              // FP32 shadow or null
-  __nv_bfloat16* Fsh;      // BF16 split history [3][n_tiles*32*D][fsh_ld] (K-major) or null
-  long long fsh_ld;        // history rows per column of Fsh
+  __nv_bfloat16* Fsh;      // BF16 split history or null, K-block tiled: piece p, column tile t,
+                           // K block kb = k / 64 is the contiguous [96 columns][64 rows] block
+                           // at ((t * fsh_ld / 64 + kb) * 96 + col) * 64 + k % 64
+  long long fsh_ld;        // history rows per column of Fsh (a multiple of 64)
   long long fsh_plane;     // elements per split piece
   double* far;             // [ksplit][n_tiles][2][B][32*D]
   // outputs
@@ -56,14 +58,15 @@ struct FarTcArgs {
   const TileDesc* tiles;
   const CUtensorMap* tmapW;  // [bucket][3]: pre-expanded Toeplitz pieces hi, mid, lo
   const CUtensorMap* tmapF;  // [3]: BF16 split history pieces
-  double* far;               // [n_tiles][2][64][96] sums, zeroed before the launch; the
-                             // ksplit CTAs of a tile add their parts with FP64 atomics
+  double* far;               // [n_tiles][2][64][96] sums; ksplit > 1: zeroed before the
+                             // launch, the CTAs of a tile add their parts with FP64 atomics
   unsigned long long* status;
   long long s;               // time tile start (multiple of 64)
   long long Lbase;           // x offset base of the pre-expanded Toeplitz
   long long budget;          // clock cycles per bounded wait
   int n_tiles;
   int ksplit;
+  int f_kblocks;             // 64-row K blocks per column tile in the history pieces
 };
 
 // Arguments of the adjoint kernels (adjoint.cu).

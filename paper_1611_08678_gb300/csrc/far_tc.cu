@@ -12,12 +12,17 @@
 // c_n f_0) are added in FP64 by the near kernel.
 //
 // Operands in HBM, both K-major so that a TMA box lands in the 128-byte
-// swizzled layout the MMA reads:
-//   W: "pre-expanded" Toeplitz, Wx[p][r][x] = piece p of w_r(Lbase - x + r%64),
-//      so the tile of time tile s and history block k0 is the plain box at
-//      x = Lbase - s + k0 (a Toeplitz tile is a shifted window of one vector;
-//      storing 128 shifted copies turns it into a regular 2D tile).
-//   F: Fsh[p][t*96 + col][k], written by the near kernel.
+// swizzled layout the MMA reads, and K-block tiled: the 64 K values of one
+// row and K block are 128 contiguous bytes, and the rows of one K block are
+// contiguous, so every TMA box is a single contiguous read of 12-16 KB
+// (a row-major K-major layout scatters each box over 96-128 rows of HBM).
+//   W: "pre-expanded" Toeplitz, piece p of w_r(Lbase - x + r%64) at
+//      ((x / 64) * 128 + r) * 64 + x % 64, so the tile of time tile s and
+//      history block k0 is the block x = Lbase - s + k0 (a Toeplitz tile is a
+//      shifted window of one vector; storing 128 shifted copies turns it into
+//      a regular 2D tile).
+//   F: history pieces, block (t, k / 64) = [96 columns][64 rows], written by
+//      the near kernel at the end of each time tile.
 // Split precision: x = x_hi + x_mid + x_lo, each BF16 (successive residuals).
 //   NPROD = 3: hi*hi + hi*mid + mid*hi      (BF16x3 mode)
 //   NPROD = 6: + hi*lo + mid*mid + lo*hi     (BF16x6 mode, FP32-level error)
@@ -58,10 +63,10 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16& hi, __nv_bfloat1
 // Pre-expanded Toeplitz weights of one alpha: Wx[p][r][x], p = hi/mid/lo.
 __global__ void build_wx_kernel(const double* __restrict__ b, const double* __restrict__ a, long long Mw,
                                 long long Lbase, long long Lx, __nv_bfloat16* __restrict__ Wx) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // output order
   if (idx >= 128 * Lx) return;
-  const int r = (int)(idx / Lx);
-  const long long x = idx % Lx;
+  const int r = (int)((idx >> 6) & 127);
+  const long long x = (idx >> 13) * 64 + (idx & 63);
   const long long lag = Lbase - x + (r & 63);
   double w = 0.0;
   if (lag >= 0 && lag <= Mw) w = (r < 64) ? b[lag] : a[lag];
@@ -114,7 +119,9 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       const CUtensorMap* mW = A.tmapW + bucket * 3;
       for (int p = 0; p < NA; ++p) tc::prefetch_tmap(mW + p);
       for (int p = 0; p < NB; ++p) tc::prefetch_tmap(A.tmapF + p);
-      const int ycol = tile * NCOL;
+      // box coordinates of history block kb: Toeplitz block x = Lbase - s + 64 kb, history block (tile, kb)
+      auto yw = [&](int kb) { return ((int)((A.Lbase - A.s) / KB) + kb) * 128; };
+      auto yf = [&](int kb) { return (tile * A.f_kblocks + kb) * NCOL; };
       for (int i = 0; i < nkb; ++i) {
         const int st = i % STAGES;
         if (i >= STAGES && !tc::mbar_wait(&empty[st], ((i / STAGES) - 1) & 1, A.budget, &abort_flag)) {
@@ -127,10 +134,10 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
         }
         uint8_t* sb = smem + st * STAGE_BYTES;
         tc::mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-        const int k0 = (kb_begin + i) * KB;
-        const int xw = (int)(A.Lbase - A.s) + k0;
-        for (int p = 0; p < NA; ++p) tc::tma_load_2d(sb + p * A_BYTES, mW + p, &full[st], xw, 0);
-        for (int p = 0; p < NB; ++p) tc::tma_load_2d(sb + NA * A_BYTES + p * B_BYTES, A.tmapF + p, &full[st], k0, ycol);
+        const int kb = kb_begin + i;
+        for (int p = 0; p < NA; ++p) tc::tma_load_2d(sb + p * A_BYTES, mW + p, &full[st], 0, yw(kb));
+        for (int p = 0; p < NB; ++p)
+          tc::tma_load_2d(sb + NA * A_BYTES + p * B_BYTES, A.tmapF + p, &full[st], 0, yf(kb));
       }
     }
   } else if (warp == 1) {
@@ -222,12 +229,18 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
     }
     if (ok && nkb > 0) {
-      // the K-split CTAs of a tile add into one FP64 sum (zeroed before the launch)
+      // the K-split CTAs of a tile add into one FP64 sum (zeroed before the
+      // launch); an unsplit tile stores its sum
       const int r = lq * 32 + lane;    // accumulator row: 0..63 predictor, 64..127 corrector
       const int half = r >> 6, i = r & 63;
       double* out = A.far + (((size_t)tile * 2 + half) * 64 + i) * NCOL + ch * 48;
+      if (A.ksplit == 1) {
 #pragma unroll
-      for (int j = 0; j < 48; ++j) atomicAdd(out + j, (double)hi[j] + (double)lo[j]);
+        for (int j = 0; j < 48; ++j) out[j] = (double)hi[j] + (double)lo[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 48; ++j) atomicAdd(out + j, (double)hi[j] + (double)lo[j]);
+      }
     }
   }
   tc::fence_before_sync();
@@ -238,14 +251,14 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
 // Diagnostic path (abm_far_history): split rows [0, s) of a caller's FP64
 // history F (rows x 96) into the BF16 planes of column tile 0 (row 0 zero).
 __global__ void fill_fsh_kernel(const double* __restrict__ F, long long s, __nv_bfloat16* __restrict__ Fsh,
-                                long long ld, long long plane) {
+                                long long plane) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= s * NCOL) return;
   const long long k = idx / NCOL;
   const int col = (int)(idx % NCOL);
   __nv_bfloat16 hi, mid, lo;
   split3(k == 0 ? 0.0 : F[idx], hi, mid, lo);
-  const size_t o = (size_t)col * ld + k;
+  const size_t o = ((size_t)(k >> 6) * NCOL + col) * 64 + (k & 63);  // K-block tiled, column tile 0
   Fsh[o] = hi;
   Fsh[plane + o] = mid;
   Fsh[2 * plane + o] = lo;
@@ -260,10 +273,9 @@ __global__ void sum_partials_kernel(const double* __restrict__ far, int ksplit, 
   (half == 0 ? P : C)[rem] = far[(size_t)half * 64 * NCOL + rem];
 }
 
-cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long ld, long long plane,
-                            cudaStream_t st) {
+cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long plane, cudaStream_t st) {
   long long n = s * NCOL;
-  fill_fsh_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, s, Fsh, ld, plane);
+  fill_fsh_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, s, Fsh, plane);
   return cudaGetLastError();
 }
 
@@ -307,6 +319,7 @@ cudaError_t launch_far_tc(int nprod, const FarTcArgs& A, int n_active, cudaStrea
 }
 
 // Host: 2D tiled tensor map, BF16, 128-byte swizzle, box {64, box_rows}.
+// With inner = 64 it walks a K-block tiled operand as [rows][64].
 bool make_tmap_bf16(CUtensorMap* out, void* base, unsigned long long inner, unsigned long long rows,
                     unsigned box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;

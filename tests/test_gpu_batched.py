@@ -157,3 +157,75 @@ def test_batched_graph_capture_replays_identically(abm):
     Y.zero_()
     g.solve_batched(batch.alpha, batch.h, N2, params, y0, Y=Y, ldY=701)
     assert np.array_equal(Y.cpu().numpy()[1:], Yr[1:]) and np.array_equal(Y.cpu().numpy()[0, :151], Yr[0, :151])
+
+
+def test_batched_edge_cases(abm):
+    """M = 1, N = 1, N not a multiple of the tile, N spanning exactly one tile,
+    alpha = 1 (trapezoid weights), one trajectory per alpha group."""
+    sysname = "lorenz"
+    cases = [
+        (np.array([1.0]), np.array([0.01]), np.array([1])),
+        (np.array([0.9, 1.0]), np.array([0.01, 0.02]), np.array([64, 65])),
+        (np.array([0.7, 0.8, 0.9, 1.0]), np.array([0.01] * 4), np.array([63, 129, 1, 200])),
+    ]
+    for prec in ("fp64", "bf16x6"):
+        for alpha, h, N in cases:
+            M = len(alpha)
+            rng = np.random.default_rng(1611)
+            params = np.array([10.0, 28.0, 8.0 / 3.0]) + rng.normal(0, 0.1, (M, 3))
+            y0 = np.array([0.1, 0.1, 0.1]) + rng.normal(0, 0.01, (M, 3))
+            plan = abm.Plan(sysname, n_max=int(N.max()), max_batch=M, prec=prec)
+            Y = plan.solve_batched(alpha, h, N, params, y0).cpu().numpy()
+            for i in range(M):
+                Yo, _ = oracle.solve(sysname, alpha[i], h[i], int(N[i]), params[i], y0[i])
+                tol = 1e-11 if prec == "fp64" else 1e-6
+                assert rel_err(Y[i, : int(N[i]) + 1], Yo) <= tol, (prec, alpha[i], N[i])
+
+
+def test_tensor_core_plan_rejects_scalar_systems(abm):
+    with pytest.raises(abm.AbmError) as ei:
+        abm.Plan("linear", n_max=100, max_batch=10, prec="bf16x6")
+    assert ei.value.status == 6
+
+
+@pytest.mark.parametrize("system", ["linear", "manufactured"])
+def test_batched_scalar_systems_fp64_and_fp32(abm, system):
+    if system == "linear":
+        batch = workloads.random_batch("linear", 50, 1, 500, [0.3, 0.6, 1.0])
+    else:
+        batch = workloads.random_batch("linear", 20, 100, 400, [0.5, 0.9])
+        import math
+        p = []
+        for a in batch.alpha:
+            c1, c2, c3, e0 = 1.0, -0.5, 0.3, 0.2
+            p.append([c1 * math.gamma(1 + a), c2 * math.gamma(2 + a), c3 * math.gamma(3 + a) / 2, -1.0, -0.5,
+                      e0, c1, c2, c3])
+        batch = workloads.Batch("manufactured", batch.alpha, batch.h, batch.N, np.array(p),
+                                np.full((batch.M, 1), 0.2), "manufactured")
+    Y = _run(abm, batch, "fp64").cpu().numpy()
+    errs = _errors(batch, Y)
+    assert errs.max() <= 1e-11, (system, errs.max())
+    # FP32 far history: the error is of order 2^-24 times the history terms,
+    # so it is measured normwise per trajectory (the pointwise measure divides
+    # by |y_n| near the zero crossings of these scalar solutions)
+    Y = _run(abm, batch, "fp32").cpu().numpy()
+    worst = 0.0
+    for i in range(batch.M):
+        N = int(batch.N[i])
+        Yo, _ = oracle.solve(batch.system, batch.alpha[i], batch.h[i], N, batch.params[i], batch.y0[i])
+        worst = max(worst, float(np.abs(Y[i, : N + 1] - Yo).max() / np.abs(Yo).max()))
+    assert worst <= 1e-6, (system, worst)
+
+
+@pytest.mark.parametrize("near_warps", [1, 2, 3, 5])
+@pytest.mark.parametrize("prec,far_split", [("fp64", 0), ("bf16x6", 1), ("bf16x6", 4)])
+def test_batched_launch_shapes(abm, near_warps, prec, far_split):
+    """Every near-kernel shape (helper warps per component) and tensor-core
+    history split gives the oracle's trajectories: the shapes the autotuner
+    picks between change the schedule, not the result."""
+    batch = workloads.random_batch("rossler", 70, 64, 700, [0.9, 1.0])
+    plan = abm.Plan(batch.system, n_max=int(batch.N.max()), max_batch=batch.M, prec=prec,
+                    near_warps=near_warps, far_split=far_split)
+    Y = plan.solve_batched(batch.alpha, batch.h, batch.N, batch.params, batch.y0).cpu().numpy()
+    errs = _errors(batch, Y, t_max=5.0)
+    assert errs.max() <= (1e-11 if prec == "fp64" else 1e-6), (near_warps, prec, far_split, errs.max())
