@@ -170,6 +170,25 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
                              const int* N, const double* params, const double* y0, double* Y,
                              long long ldY, double* YP, void* stream);
 
+/* abm_solve_batched with HOST buffers (the paper has no counterpart: it is
+ * the call a user makes with inputs and results in host memory).  alpha, h,
+ * N as above; params (M x nparams) and y0 (M x d) are read from host memory,
+ * and trajectory i's rows 0..N[i] of Y (and YP when not NULL), laid out as in
+ * abm_solve_batched with leading dimension ldY, are written to host memory;
+ * the rest of Y is left untouched.  The inputs are copied up on `stream`
+ * first.  Each trajectory's rows are copied down on a stream of the plan as
+ * soon as the time tile that finishes it has run, overlapping the remaining
+ * time tiles.  The call's work, copies included, is complete once `stream`
+ * has passed it (abm_plan_sync).  The host arrays must stay valid until then
+ * and should be page-locked (cudaHostAlloc / cudaHostRegister): with pageable
+ * memory the copies still happen but stop overlapping.  The first call
+ * allocates the plan's device copies of params, y0 and Y (max_batch rows of
+ * n_max+1 steps each) and a copy stream; later calls reuse them, so calls on
+ * one plan must not run concurrently.  Never captured in a CUDA graph. */
+abm_status abm_solve_batched_host(abm_plan p, int M, const double* alpha, const double* h,
+                                  const int* N, const double* params, const double* y0, double* Y,
+                                  long long ldY, double* YP, void* stream);
+
 /* Adjoint of abm_solve_batched (the discrete adjoint of exactly the scheme
  * above; the paper has no adjoint).  The arguments alpha .. ldY must be those
  * of a completed abm_solve_batched call on this plan whose outputs Y and YP

@@ -23,7 +23,7 @@ STATUS = {0: "ABM_OK", 1: "ABM_ERR_INVALID_ARG", 2: "ABM_ERR_CUDA", 3: "ABM_ERR_
 # Every symbol include/abm.h declares (checked by the CPU test suite).
 EXPORTS = ["abm_plan_opts_default", "abm_system_dim", "abm_system_nparams", "abm_plan_create",
            "abm_plan_destroy", "abm_plan_sync", "abm_last_error", "abm_weights", "abm_solve",
-           "abm_solve_batched", "abm_adjoint", "abm_far_history", "abm_solve_noalloc",
+           "abm_solve_batched", "abm_solve_batched_host", "abm_adjoint", "abm_far_history", "abm_solve_noalloc",
            "abm_plan_kernel_times"]
 KERNEL_KINDS = {"weights": 0, "far": 1, "near": 2, "single": 3, "adjoint": 4}
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         lib.abm_weights.argtypes = [_vp, D, I, _vp, _vp, _vp, _vp]
         lib.abm_solve.argtypes = [_vp, D, D, I, _dp, _dp, _vp, _vp, _vp]
         lib.abm_solve_batched.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
+        lib.abm_solve_batched_host.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_adjoint.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp, _vp, _vp]
         lib.abm_far_history.argtypes = [_vp, D, _vp, LL, LL, LL, I, LL, LL, _vp, _vp, _vp]
         lib.abm_plan_kernel_times.argtypes = [_vp, I, _vp, I, ctypes.POINTER(LL), ctypes.POINTER(D)]
@@ -224,6 +225,44 @@ class Plan:
                                         NN.ctypes.data_as(_ip), _dptr(params), _dptr(y0), _dptr(Y), int(ldY),
                                         _dptr(YP), _stream_ptr(stream))
         self._check(st, "abm_solve_batched")
+        if sync:
+            self.sync(stream)
+        return (Y, YP) if want_yp or YP is not None else Y
+
+    def solve_batched_host(self, alpha, h, N, params, y0, Y=None, YP=None, want_yp=False, ldY=None,
+                           stream=None, sync=True):
+        """abm_solve_batched_host: params (M, np), y0 (M, d) and the results Y
+        (M, ldY, d) [and YP] in host memory (torch CPU tensors, page-locked
+        when allocated here); the library copies inputs up and each finished
+        trajectory down while later time tiles run."""
+        torch = _torch()
+        al = np.ascontiguousarray(alpha, dtype=np.float64)
+        hh = np.ascontiguousarray(h, dtype=np.float64)
+        NN = np.ascontiguousarray(N, dtype=np.int32)
+        M = al.size
+        params = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float64)) if not torch.is_tensor(params) \
+            else params
+        y0 = torch.as_tensor(np.ascontiguousarray(y0, dtype=np.float64)) if not torch.is_tensor(y0) else y0
+        if params.is_cuda or y0.is_cuda:
+            raise ValueError("solve_batched_host takes host tensors; use solve_batched for device tensors")
+        params = params.to(torch.float64).contiguous()
+        y0 = y0.to(torch.float64).contiguous()
+        if ldY is None:
+            ldY = int(NN.max()) + 1
+        if Y is None:
+            Y = torch.zeros(M, ldY, self.d, dtype=torch.float64, pin_memory=True)
+        if YP is None and want_yp:
+            YP = torch.zeros(M, ldY, self.d, dtype=torch.float64, pin_memory=True)
+        for t in (Y, YP):
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise ValueError("Y / YP must be contiguous host tensors")
+        self._host_inputs = (params, y0)  # read by the asynchronous upload
+        st = self.lib.abm_solve_batched_host(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
+                                             NN.ctypes.data_as(_ip), ctypes.c_void_p(params.data_ptr()),
+                                             ctypes.c_void_p(y0.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                             int(ldY), ctypes.c_void_p(YP.data_ptr()) if YP is not None else None,
+                                             _stream_ptr(stream))
+        self._check(st, "abm_solve_batched_host")
         if sync:
             self.sync(stream)
         return (Y, YP) if want_yp or YP is not None else Y

@@ -105,6 +105,11 @@ struct abm_plan_s {
   CUtensorMap* d_tmapX = nullptr;   // [3]
   TileDesc* d_atiles = nullptr;     // [2 * max_tiles]
   double *acc_dp = nullptr, *acc_dy0 = nullptr, *phi0c = nullptr;
+  // host-buffer batched solve (abm_solve_batched_host; allocated by its first call)
+  double *hio_params = nullptr, *hio_y0 = nullptr, *hio_Y = nullptr, *hio_YP = nullptr;
+  cudaStream_t copy_st = nullptr;
+  std::vector<cudaEvent_t> hio_ev;  // per time tile in which trajectories finish
+  cudaEvent_t hio_done = nullptr;
   // CUDA graph of the batched launch sequence (opts.use_graph)
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<unsigned char> graph_key;
@@ -372,9 +377,23 @@ abm_status schedule_batch(abm_plan p, int M, const double* alpha, const double* 
   return ABM_OK;
 }
 
+// Copy-out of finished trajectories to host memory while later time tiles
+// run (abm_solve_batched_host): by_tile[j] lists the trajectories whose last
+// row N_i is written by the near kernel of time tile j.
+struct HostCopyOut {
+  std::vector<std::vector<int>> by_tile;
+  const int* N = nullptr;
+  double *Yh = nullptr, *YPh = nullptr;  // host, leading dimension ldh
+  long long ldh = 0;
+  const double *Yd = nullptr, *YPd = nullptr;  // device, leading dimension ldd
+  long long ldd = 0;
+};
+
 // The far / near launch sequence of one batched solve on stream st (tables
-// already on the device).
-abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t st) {
+// already on the device); with out, each time tile's finished trajectories
+// are copied to the host on the plan's copy stream behind that tile.
+abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t st,
+                           const HostCopyOut* out = nullptr) {
   const int B = p->B, d = p->d;
   const bool tc_prec = p->Fsh != nullptr;
   const std::vector<TileDesc>& tiles = S.tiles;
@@ -414,8 +433,56 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
                                       : (n_active <= p->sms ? 3 : (n_active <= 2 * p->sms ? 2 : 1));
       CK(launch_batched_near(p->sys, A, n_active, s, B, wpc, st), "near kernel");
     }
+    if (out && j < (int)out->by_tile.size() && !out->by_tile[j].empty()) {
+      cudaEvent_t ev = p->hio_ev[j];
+      CK(cudaEventRecord(ev, st), "event");
+      CK(cudaStreamWaitEvent(p->copy_st, ev, 0), "event wait");
+      for (int i : out->by_tile[j]) {
+        const size_t bytes = (size_t)(out->N[i] + 1) * d * sizeof(double);
+        CK(cudaMemcpyAsync(out->Yh + (size_t)i * out->ldh * d, out->Yd + (size_t)i * out->ldd * d, bytes,
+                           cudaMemcpyDeviceToHost, p->copy_st), "copy-out");
+        if (out->YPh)
+          CK(cudaMemcpyAsync(out->YPh + (size_t)i * out->ldh * d, out->YPd + (size_t)i * out->ldd * d, bytes,
+                             cudaMemcpyDeviceToHost, p->copy_st), "copy-out");
+      }
+    }
   }
   return ABM_OK;
+}
+
+// Kernel arguments of one batched solve (tables from schedule_batch).
+BatchArgs batch_args(abm_plan p, const Sched& S, const double* params, const double* y0, double* Y, double* YP,
+                     long long ldY) {
+  const int d = p->d;
+  BatchArgs A{};
+  A.tiles = p->d_tiles;
+  A.n_tiles = S.n_tiles;
+  A.B = p->B;
+  A.ksplit = S.ksplit;
+  A.far_k0 = 1;
+  A.bucket_alpha = p->d_balpha;
+  A.bucket_b = p->d_bptr;
+  A.bucket_a = p->d_bptr + kMaxWeightSets;
+  A.bucket_c = p->d_bptr + 2 * kMaxWeightSets;
+  A.bucket_b32 = p->d_b32ptr;
+  A.bucket_a32 = p->d_b32ptr + kMaxWeightSets;
+  A.bucket_g = p->d_bg;
+  A.h = p->d_h;
+  A.N = p->d_N;
+  A.params = params;
+  A.y0 = y0;
+  A.hhat = p->d_hhat;
+  A.F = p->Fb;
+  A.F32 = (p->o.prec == ABM_PREC_FP32_FAR) ? p->Fb32 : nullptr;
+  A.Fsh = p->Fsh;
+  A.fsh_ld = p->fsh_ld;
+  A.fsh_plane = (long long)p->max_tiles * kTrajPerTile * d * p->fsh_ld;
+  A.far = p->farb;
+  A.Y = Y;
+  A.YP = YP;
+  A.ldY = ldY;
+  A.status = p->status;
+  return A;
 }
 
 template <typename T>
@@ -544,6 +611,10 @@ abm_status abm_plan_destroy(abm_plan p) {
   cudaFree(p->Xadj); cudaFree(p->Xsh); cudaFree(p->d_tmapX); cudaFree(p->d_atiles);
   cudaFree(p->acc_dp); cudaFree(p->acc_dy0); cudaFree(p->phi0c);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  cudaFree(p->hio_params); cudaFree(p->hio_y0); cudaFree(p->hio_Y); cudaFree(p->hio_YP);
+  for (cudaEvent_t e : p->hio_ev) cudaEventDestroy(e);
+  if (p->hio_done) cudaEventDestroy(p->hio_done);
+  if (p->copy_st) cudaStreamDestroy(p->copy_st);
   cudaFree(p->ppartial); cudaFree(p->pflags);
   cudaFree(p->F1); cudaFree(p->far1); cudaFree(p->part1); cudaFree(p->tickets); cudaFree(p->hhat1);
   cudaFree(p->Fb); cudaFree(p->Fb32); cudaFree(p->farb); cudaFree(p->d_tiles); cudaFree(p->d_h);
@@ -687,38 +758,10 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
       return ABM_OK;
     }
   }
-  const int B = p->B, d = p->d;
   Sched S;
   abm_status rs = schedule_batch(p, M, alpha, h, N, ldY, st, S, "abm_solve_batched");
   if (rs) return rs;
-  BatchArgs A{};
-  A.tiles = p->d_tiles;
-  A.n_tiles = S.n_tiles;
-  A.B = B;
-  A.ksplit = S.ksplit;
-  A.far_k0 = 1;
-  A.bucket_alpha = p->d_balpha;
-  A.bucket_b = p->d_bptr;
-  A.bucket_a = p->d_bptr + kMaxWeightSets;
-  A.bucket_c = p->d_bptr + 2 * kMaxWeightSets;
-  A.bucket_b32 = p->d_b32ptr;
-  A.bucket_a32 = p->d_b32ptr + kMaxWeightSets;
-  A.bucket_g = p->d_bg;
-  A.h = p->d_h;
-  A.N = p->d_N;
-  A.params = params;
-  A.y0 = y0;
-  A.hhat = p->d_hhat;
-  A.F = p->Fb;
-  A.F32 = (p->o.prec == ABM_PREC_FP32_FAR) ? p->Fb32 : nullptr;
-  A.Fsh = p->Fsh;
-  A.fsh_ld = p->fsh_ld;
-  A.fsh_plane = (long long)p->max_tiles * kTrajPerTile * d * p->fsh_ld;
-  A.far = p->farb;
-  A.Y = Y;
-  A.YP = YP;
-  A.ldY = ldY;
-  A.status = p->status;
+  const BatchArgs A = batch_args(p, S, params, y0, Y, YP, ldY);
   if (!p->o.use_graph) return enqueue_batched(p, S, A, st);
   // capture the launch sequence on the plan's side stream, after the uploads
   if (p->graph_exec) {
@@ -740,6 +783,55 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
   if (ce != cudaSuccess) { p->graph_exec = nullptr; return cuda_fail(p, ce, "graph instantiate"); }
   p->graph_key = key;
   CK(cudaGraphLaunch(p->graph_exec, st), "graph launch");
+  return ABM_OK;
+}
+
+abm_status abm_solve_batched_host(abm_plan p, int M, const double* alpha, const double* h, const int* N,
+                                  const double* params, const double* y0, double* Y, long long ldY, double* YP,
+                                  void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched_host: need 1 <= M <= max_batch and non-null arrays");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = p->d, B = p->B;
+  const long long ldd = (long long)p->o.n_max + 1;  // leading dimension of the device copy of Y
+  // device buffers and the copy stream, once per plan
+  if (!p->hio_Y) {
+    CK(cudaMalloc(&p->hio_params, (size_t)p->o.max_batch * std::max(1, p->np) * sizeof(double)), "host-io params");
+    CK(cudaMalloc(&p->hio_y0, (size_t)p->o.max_batch * d * sizeof(double)), "host-io y0");
+    CK(cudaMalloc(&p->hio_Y, (size_t)p->o.max_batch * ldd * d * sizeof(double)), "host-io Y");
+    CK(cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking), "copy stream");
+    CK(cudaEventCreateWithFlags(&p->hio_done, cudaEventDisableTiming), "event");
+  }
+  if (YP && !p->hio_YP) CK(cudaMalloc(&p->hio_YP, (size_t)p->o.max_batch * ldd * d * sizeof(double)), "host-io YP");
+  Sched S;
+  abm_status rs = schedule_batch(p, M, alpha, h, N, ldY, st, S, "abm_solve_batched_host");
+  if (rs) return rs;
+  // inputs up, then the solve with each finished trajectory copied out behind
+  // the time tile that completes it
+  CK(cudaMemcpyAsync(p->hio_params, params, (size_t)M * p->np * sizeof(double), cudaMemcpyHostToDevice, st),
+     "params upload");
+  CK(cudaMemcpyAsync(p->hio_y0, y0, (size_t)M * d * sizeof(double), cudaMemcpyHostToDevice, st), "y0 upload");
+  HostCopyOut out;
+  out.by_tile.assign((S.nmax + B - 1) / B, {});
+  for (int i = 0; i < M; ++i) out.by_tile[(N[i] - 1) / B].push_back(i);
+  while (p->hio_ev.size() < out.by_tile.size()) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    p->hio_ev.push_back(e);
+  }
+  out.N = N;
+  out.Yh = Y;
+  out.YPh = YP;
+  out.ldh = ldY;
+  out.Yd = p->hio_Y;
+  out.YPd = YP ? p->hio_YP : nullptr;
+  out.ldd = ldd;
+  const BatchArgs A = batch_args(p, S, p->hio_params, p->hio_y0, p->hio_Y, YP ? p->hio_YP : nullptr, ldd);
+  rs = enqueue_batched(p, S, A, st, &out);
+  if (rs) return rs;
+  CK(cudaEventRecord(p->hio_done, p->copy_st), "event");
+  CK(cudaStreamWaitEvent(st, p->hio_done, 0), "event wait");  // the call's work ends on st
   return ABM_OK;
 }
 
@@ -827,7 +919,7 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
   AdjArgs A{};
   A.tiles = p->d_tiles;
   A.atiles = p->d_atiles;
-  A.B = B;
+  A.B = p->B;
   A.bucket_alpha = p->d_balpha;
   A.bucket_b = p->d_bptr;
   A.bucket_a = p->d_bptr + kMaxWeightSets;

@@ -26,11 +26,17 @@
 // Split precision: x = x_hi + x_mid + x_lo, each BF16 (successive residuals).
 //   NPROD = 3: hi*hi + hi*mid + mid*hi      (BF16x3 mode)
 //   NPROD = 6: + hi*lo + mid*mid + lo*hi     (BF16x6 mode, FP32-level error)
-// The leading product hi*hi and the correction products accumulate in two
+// The leading product hi*hi and the correction products accumulate in
 // separate TMEM accumulators (so the small corrections are not added into a
-// large running sum), each over at most CHUNK_BLOCKS*64 history rows; each
-// chunk is then added into a compensated FP32 pair (TwoSum) by the epilogue
-// warps while the MMAs fill the other TMEM buffer pair.
+// large running sum).  The tensor core's FP32 accumulation of the leading
+// product loses precision with every MMA it adds, so in BF16x6 mode its
+// accumulator holds one 64-row K block only (CB = 1): three buffers rotate,
+// and the epilogue warps add each finished block into a compensated FP32 pair
+// (TwoSum) while the MMAs fill the next (measured on Rossler: pointwise error
+// 9e-7 with 128-256 rows per accumulator, 2e-7 with 64).  BF16x3 drops
+// products of order 2^-16, far above that loss, and keeps CB = 4 blocks (256
+// rows).  The corrections, 2^-8 of the leading term, accumulate in TMEM over
+// the CTA's whole history range and are added once.
 //
 // Warp roles (320 threads): warp 0 TMA producer, warp 1 TMEM owner + MMA
 // issuer, warps 2..9 epilogue (lane quarter = warp % 4, column half = (warp-2)/4).
@@ -45,7 +51,8 @@ namespace abm {
 
 namespace {
 constexpr int KB = 64;          // history rows per K block (128 bytes of BF16)
-constexpr int CHUNK_BLOCKS = 4; // K blocks per FP32 accumulation chunk (256 rows)
+constexpr int MAIN_BUFS = 3;    // TMEM buffers of the leading-product accumulator
+constexpr uint32_t CORR_COL = MAIN_BUFS * 128;  // TMEM column of the correction accumulator
 constexpr int NCOL = 96;        // columns per tile (32 trajectories x 3)
 constexpr int A_BYTES = 128 * KB * 2;
 constexpr int B_BYTES = NCOL * KB * 2;
@@ -85,9 +92,10 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
   constexpr int NB = NA;                  // F pieces used
   constexpr int STAGES = NPROD == 3 ? 3 : 2;
   constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
+  constexpr int CB = NPROD == 3 ? 4 : 1;  // K blocks per leading-product accumulator
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], mma_done;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[MAIN_BUFS], acc_empty[MAIN_BUFS], mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
 
@@ -98,13 +106,13 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
   const int per_q = (nkb_total + A.ksplit - 1) / A.ksplit;
   const int kb_begin = q * per_q;
   const int nkb = max(0, min(nkb_total, kb_begin + per_q) - kb_begin);
-  const int nchunks = (nkb + CHUNK_BLOCKS - 1) / CHUNK_BLOCKS;
+  const int nchunks = (nkb + CB - 1) / CB;
 
   if (tid == 0) abort_flag = 0;
   if (warp == 1) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
     for (int i = 0; i < STAGES; ++i) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
-    for (int i = 0; i < 2; ++i) { tc::mbar_init(&acc_full[i], 1); tc::mbar_init(&acc_empty[i], 8); }
+    for (int i = 0; i < MAIN_BUFS; ++i) { tc::mbar_init(&acc_full[i], 1); tc::mbar_init(&acc_empty[i], 8); }
     tc::mbar_init(&mma_done, 1);
     tc::fence_mbar_init();
   }
@@ -147,19 +155,20 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       // (A piece, B piece) of each product: hi=0, mid=1, lo=2
       constexpr int PA[6] = {0, 0, 1, 0, 1, 2};
       constexpr int PB[6] = {0, 1, 0, 2, 1, 0};
-      int i = 0;
+      const uint32_t d_corr = tmem + CORR_COL;
+      bool first_corr = true;
+      int i = 0;  // K block
       for (int c = 0; c < nchunks && !abort_flag; ++c) {
-        const int buf = c & 1;
-        if (c >= 2 && !tc::mbar_wait(&acc_empty[buf], ((c / 2) - 1) & 1, A.budget, &abort_flag)) {
+        const int buf = c % MAIN_BUFS, use = c / MAIN_BUFS;
+        if (use >= 1 && !tc::mbar_wait(&acc_empty[buf], (use - 1) & 1, A.budget, &abort_flag)) {
           abort_flag = 1;
           report_status(A.status, ABM_ERR_TIMEOUT, tile, 2000 + c);
           break;
         }
         tc::fence_after_sync();
-        const uint32_t d_main = tmem + buf * 256, d_corr = d_main + 128;
-        const int iend = min(nkb, (c + 1) * CHUNK_BLOCKS);
-        bool first_main = true, first_corr = true;
-        for (; i < iend; ++i) {
+        const uint32_t d_main = tmem + buf * 128;
+        bool first_main = true;
+        for (const int iend = min(nkb, (c + 1) * CB); i < iend; ++i) {
           const int st = i % STAGES;
           if (!tc::mbar_wait(&full[st], (i / STAGES) & 1, A.budget, &abort_flag)) {
             abort_flag = 1;
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
           }
           tc::mma_commit(&empty[st]);  // stage reusable once these MMAs have read it
         }
-        tc::mma_commit(&acc_full[buf]);  // chunk accumulator complete
+        tc::mma_commit(&acc_full[buf]);  // this chunk's leading-product sum is complete
       }
       // every MMA this thread issued has completed before TMEM is released
       tc::mma_commit(&mma_done);
@@ -196,39 +205,53 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
     // ---------------- epilogue: 8 warps ----------------
     const int lq = warp & 3;           // TMEM lane quarter this warp may access
     const int ch = (warp - 2) >> 2;    // column half: 0 -> cols 0..47, 1 -> 48..95
+    const uint32_t lane_base = tmem + ((uint32_t)(lq * 32) << 16) + ch * 48;
     float hi[48], lo[48];
 #pragma unroll
     for (int j = 0; j < 48; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
-      const int buf = c & 1;
-      if (!tc::mbar_wait(&acc_full[buf], (c / 2) & 1, A.budget, &abort_flag)) {
+      const int buf = c % MAIN_BUFS;
+      if (!tc::mbar_wait(&acc_full[buf], (c / MAIN_BUFS) & 1, A.budget, &abort_flag)) {
         ok = false;
         break;
       }
       tc::fence_after_sync();
-      const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + buf * 256 + ch * 48;
+      uint32_t v[3][16];  // the chunk's leading products: three loads in flight, one wait
+#pragma unroll
+      for (int g16 = 0; g16 < 3; ++g16) tc::tmem_ld_32x16_issue(lane_base + buf * 128 + g16 * 16, v[g16]);
+#pragma unroll
+      for (int g16 = 0; g16 < 3; ++g16) tc::tmem_ld_wait16(v[g16]);
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);  // values are in registers
+#pragma unroll
+      for (int g16 = 0; g16 < 3; ++g16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {  // (hi, lo) += v  (TwoSum)
+          const int jj = g16 * 16 + j;
+          const float x = __uint_as_float(v[g16][j]);
+          const float s = hi[jj] + x;
+          const float bp = s - hi[jj];
+          lo[jj] += (hi[jj] - (s - bp)) + (x - bp);
+          hi[jj] = s;
+        }
+      }
+    }
+    // the correction products, accumulated over the whole range: into lo
+    if (ok && nkb > 0 && tc::mbar_wait(&mma_done, 0, A.budget, &abort_flag)) {
+      tc::fence_after_sync();
 #pragma unroll
       for (int g16 = 0; g16 < 3; ++g16) {
         float v[16];
-        tc::tmem_ld_32x16(base + g16 * 16, v);  // leading products
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {  // (hi, lo) += main  (TwoSum)
-          const int jj = g16 * 16 + j;
-          const float s = hi[jj] + v[j];
-          const float bp = s - hi[jj];
-          lo[jj] += (hi[jj] - (s - bp)) + (v[j] - bp);
-          hi[jj] = s;
-        }
-        tc::tmem_ld_32x16(base + 128 + g16 * 16, v);  // correction products, small: into lo
+        tc::tmem_ld_32x16(lane_base + CORR_COL + g16 * 16, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) lo[g16 * 16 + j] += v[j];
       }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+    } else {
+      ok = false;
     }
-    if (ok && nkb > 0) {
+    if (ok) {
       // the K-split CTAs of a tile add into one FP64 sum (zeroed before the
       // launch); an unsplit tile stores its sum
       const int r = lq * 32 + lane;    // accumulator row: 0..63 predictor, 64..127 corrector

@@ -229,3 +229,30 @@ def test_batched_launch_shapes(abm, near_warps, prec, far_split):
     Y = plan.solve_batched(batch.alpha, batch.h, batch.N, batch.params, batch.y0).cpu().numpy()
     errs = _errors(batch, Y, t_max=5.0)
     assert errs.max() <= (1e-11 if prec == "fp64" else 1e-6), (near_warps, prec, far_split, errs.max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_batched_host_buffers_match_device_path(abm, prec):
+    """abm_solve_batched_host (inputs and results in host memory, copy-out
+    behind each finishing time tile) gives the device entry point's
+    trajectories, leaves rows beyond N_i untouched, and also works with
+    pageable host buffers."""
+    batch = workloads.random_batch("rossler", 70, 64, 700, [0.9, 1.0])
+    M = batch.M
+    plan = abm.Plan(batch.system, n_max=int(batch.N.max()), max_batch=M, prec=prec)
+    Yd, YPd = plan.solve_batched(batch.alpha, batch.h, batch.N, batch.params, batch.y0, want_yp=True)
+    Yd, YPd = Yd.cpu().numpy(), YPd.cpu().numpy()
+    ldY = int(batch.N.max()) + 5
+    Yh = torch.full((M, ldY, 3), -7.0, dtype=torch.float64).pin_memory()
+    YPh = torch.full((M, ldY, 3), -7.0, dtype=torch.float64).pin_memory()
+    plan.solve_batched_host(batch.alpha, batch.h, batch.N, batch.params, batch.y0, Y=Yh, YP=YPh, ldY=ldY)
+    Yp = torch.zeros(M, ldY, 3, dtype=torch.float64)  # pageable
+    plan.solve_batched_host(batch.alpha, batch.h, batch.N, torch.as_tensor(batch.params),
+                            torch.as_tensor(batch.y0), Y=Yp, ldY=ldY)
+    tol = 0.0 if prec == "fp64" else 1e-12  # split tiles add in FP64 atomics: order varies
+    for i in range(M):
+        n = int(batch.N[i])
+        for got in (Yh.numpy(), Yp.numpy()):
+            assert rel_err(got[i, : n + 1], Yd[i, : n + 1]) <= tol, (i, prec)
+        assert rel_err(YPh.numpy()[i, 1: n + 1], YPd[i, 1: n + 1]) <= tol
+        assert np.all(Yh.numpy()[i, n + 1:] == -7.0) and np.all(YPh.numpy()[i, n + 1:] == -7.0)
