@@ -57,13 +57,11 @@ NCU_TRAFFIC = {
     "chen_single": 7071488 + 95232,  # profiles/single_persistent_kernel_chen_N262144.md
 }
 # Batched far kernel: DRAM bytes (read + write) of one captured launch over the
-# algorithmic operand bytes of that launch (profiles/far_tc_kernel_rossler_batched.md:
-# 512 trajectories, time tile s = 38464, 8 active tiles in 8 alpha groups,
-# 414.4 + 2.8 MB against 413.6 MB); the bench line scales it to its own
-# average launch, since DRAM bytes grow with the operand bytes.
-NCU_TRAFFIC_RATIO = {
-    "rossler_batched_bf16x6": (414419712 + 2841600) / 413564928,
-}
+# algorithmic operand bytes of that launch, per workload and precision, from
+# an ncu capture of the current kernel; the bench line scales it to its own
+# average launch, since DRAM bytes grow with the operand bytes.  Empty until
+# the far kernel as it stands has been captured.
+NCU_TRAFFIC_RATIO = {}
 
 
 def parse_args(argv=None):
@@ -316,7 +314,18 @@ def tile_schedule(w, per_tile=32):
     return tiles
 
 
-def far_work(w, nprod, B=64):
+def tc_far(prec):
+    """Far history on the tensor cores (BF16 split pieces)."""
+    return prec in ("bf16x3", "bf16x6")
+
+
+def far_shape(prec):
+    """(split products, 16-bit pieces per operand, kernel name) of a tensor-core precision."""
+    return {"bf16x3": (3, 2, "far_tc_kernel<3> (BF16x3)"),
+            "bf16x6": (6, 3, "far_tc_kernel<6> (BF16x6)")}.get(prec, (6, 3, "far_tc_kernel<6> (BF16x6)"))
+
+
+def far_work(w, nprod, npieces=None, B=64):
     """Per whole solve: algorithmic far flops (each trajectory's own targets
     n < N_i times its far rows [1, s)), raw tensor flops the MMAs execute
     (padded 128 x 96 tiles, all split products) and the operand bytes the far
@@ -325,7 +334,7 @@ def far_work(w, nprod, B=64):
     import numpy as np
     tiles = tile_schedule(w)
     nmax = max(t[0] for t in tiles)
-    npieces = 2 if nprod == 3 else 3
+    npieces = npieces or (2 if nprod == 3 else 3)
     alg = raw = byts = 0.0
     for j in range((nmax + B - 1) // B):
         s = j * B
@@ -351,7 +360,7 @@ def bench_batched(args, name, w, prec, world, rank, local):
     N = shard.N
     ldY = int(N.max()) + 1
     tuned = {"near_warps": 0, "far_split": 0}
-    if prec.startswith("bf16") and not args.no_tune:
+    if tc_far(prec) and not args.no_tune:
         from paper_1611_08678_gb300 import autotune
         tuned = autotune.tune_batched(shard, prec)  # untimed; cached per shape
     plan = abm.Plan(shard.system, n_max=int(N.max()), max_batch=shard.M, prec=prec, profile=True,
@@ -394,17 +403,17 @@ def bench_batched(args, name, w, prec, world, rank, local):
     value = steps_all / total_max
     macs_all = w.history_macs() * args.steps
 
-    nprod = 3 if prec == "bf16x3" else 6
+    nprod, npieces, kname = far_shape(prec)
     far_n, far_ms = times["far"]
     near_n, near_ms = times["near"]
-    if prec.startswith("bf16"):
-        alg, raw, byts = far_work(shard, nprod)
+    if tc_far(prec):
+        alg, raw, byts = far_work(shard, nprod, npieces)
         far_sec = far_ms / 1e3 / args.steps  # per solve
         roof = {"bound": "hbm", "achieved": byts / far_sec / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                 "frac": byts / far_sec / 1e9 / HBM_PEAK_GBS,
                 "traffic": (NCU_TRAFFIC_RATIO[f"{name}_{prec}"] * byts / max(1, far_n / args.steps)
                             if f"{name}_{prec}" in NCU_TRAFFIC_RATIO else None),
-                "kernel": f"far_tc_kernel<{nprod}>", "launches_per_solve": far_n / args.steps,
+                "kernel": kname, "launches_per_solve": far_n / args.steps,
                 "bytes_per_launch": byts / max(1, far_n / args.steps),
                 "algorithmic_tflops": alg / far_sec / 1e12,
                 "tensor_tflops_raw": raw / far_sec / 1e12, "tensor_peak_tflops": BF16_PEAK_TFLOPS,
@@ -582,9 +591,9 @@ def bench_adjoint(args, name, prec, world, rank, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     total_max = float(t.item())
     value = float(w_all.N.sum()) * args.steps / total_max
-    nprod = 3 if prec == "bf16x3" else 6
+    nprod, npieces, kname = far_shape(prec)
     far_n, far_ms = times["far"]
-    alg, raw, byts = far_work(w, nprod)
+    alg, raw, byts = far_work(w, nprod, npieces)
     far_sec = far_ms / 1e3 / args.steps
     out = {
         "metric": "trajectory-steps/s of forward + adjoint (history MAC/s beside; gradient error vs oracle stated)",
@@ -597,7 +606,7 @@ def bench_adjoint(args, name, prec, world, rank, local):
         "history_mac_per_s": 2 * w_all.history_macs() * args.steps / total_max,
         "roofline": {"bound": "hbm", "achieved": byts / far_sec / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                      "frac": byts / far_sec / 1e9 / HBM_PEAK_GBS, "traffic": None,
-                     "kernel": f"far_tc_kernel<{nprod}> (forward launches)",
+                     "kernel": f"{kname} (forward launches)",
                      "tensor_tflops_raw": raw / far_sec / 1e12, "tensor_frac": raw / far_sec / 1e12 / BF16_PEAK_TFLOPS},
         "kernel_ms_per_solve": {k: v[1] / args.steps for k, v in times.items() if v[0]},
         "gpu_launches": int(sum(v[0] for v in times.values())),

@@ -107,8 +107,10 @@ typedef struct {
                           chain warp plus helpers that sum the next step's window
                           (lag slices) while the chain runs: 0 = chosen from the
                           active tiles, 1 (chain only), 2, 3 or 5                */
-  int far_split;       /* tensor-core far kernel: CTAs per time tile in waves of
-                          the SM count (history split across CTAs); 0 = 2        */
+  int far_split;       /* tensor-core far kernel: the history of each column tile
+                          may be split across CTAs while the launch takes at most
+                          far_split times the waves (CTAs / SM count, rounded up)
+                          of the unsplit launch; 0 = 2                           */
   int reserved[8];     /* must be zero                                            */
 } abm_plan_opts;
 

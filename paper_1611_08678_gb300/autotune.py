@@ -5,9 +5,9 @@ The kernels expose two shape knobs (include/abm.h, abm_plan_opts):
                plus helpers summing slices of the next step's window while the
                chain runs: 1 (chain only), 2 or 3 - FP64 latency per step
                against instruction count when many column tiles share an SM
-  far_split  : CTAs of the tensor-core far kernel per time tile, in waves of
-               the SM count (the history of each column tile is split across
-               that many CTAs, their parts added on the device)
+  far_split  : how far the tensor-core far kernel may split each column
+               tile's history across CTAs: at most far_split times the waves
+               of the unsplit launch (the parts are added on the device)
 The tuner times a full batched solve (CUDA events, after one warm-up) for
 each candidate and keeps the fastest.  Results are cached in a JSON file
 keyed by GPU, system, precision and the workload's shape buckets, so a later

@@ -325,6 +325,11 @@ cudaError_t launch_adjoint_near_t(const AdjArgs& A, int n_active, long long s, i
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(adjoint_near_kernel<SYS, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    // the far kernels between these launches need the largest shared-memory
+    // carveout; asking for it here too saves a reconfiguration per switch
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(adjoint_near_kernel<SYS, HS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }

@@ -26,7 +26,7 @@ cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long 
                                 cudaStream_t st);
 cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, int n_active, long long s,
                                cudaStream_t st);
-cudaError_t launch_far_tc(int nprod, const FarTcArgs& A, int n_active, cudaStream_t st);
+cudaError_t launch_far_tc(int kind, const FarTcArgs& A, int n_active, cudaStream_t st);
 cudaError_t launch_build_wx(const double* b, const double* a, long long Mw, long long Lbase, long long Lx,
                             __nv_bfloat16* Wx, cudaStream_t st);
 bool make_tmap_bf16(CUtensorMap* out, void* base, unsigned long long inner, unsigned long long rows,
@@ -225,15 +225,18 @@ abm_status get_weights(abm_plan p, double alpha, cudaStream_t st, WeightSet** ou
 // sms) waves, each as long as one CTA: a fixed part (TMEM and barrier setup,
 // pipeline fill, the FP64 reductions at the end; about kFarCtaSetupBlocks
 // K blocks of streaming) plus its ceil(nkb / ks) K blocks.  Picks the split
-// with the least modelled time among those within max_waves waves, so a
-// split never spills a few CTAs into an extra, mostly idle wave.
+// with the least modelled time among those within max_waves times the waves
+// of the unsplit launch: a split that fills a partial last wave (512 tiles
+// on 152 SMs: 3.4 waves unsplit, 6.7 split in two) is allowed, one that only
+// multiplies short CTAs is not.
 constexpr double kFarCtaSetupBlocks = 6.0;
 int far_ksplit(int n_tiles, int nkb, int sms, int max_waves) {
   int best = 1;
   double best_cost = 1e300;
+  const long long cap = (long long)max_waves * (((long long)n_tiles + sms - 1) / sms);
   for (int ks = 1; ks <= nkb; ++ks) {
     const long long waves = ((long long)n_tiles * ks + sms - 1) / sms;
-    if (ks > 1 && waves > max_waves) break;
+    if (ks > 1 && waves > cap) break;
     const double cost = (double)waves * (kFarCtaSetupBlocks + (double)((nkb + ks - 1) / ks));
     if (cost < best_cost) {
       best_cost = cost;
@@ -241,6 +244,25 @@ int far_ksplit(int n_tiles, int nkb, int sms, int max_waves) {
     }
   }
   return best;
+}
+
+// Tensor-core far kernel of the plan's precision: 3 = BF16x3, 6 = BF16x6.
+int far_kind(const abm_plan p) { return p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6; }
+
+FarTcArgs far_tc_args(abm_plan p, const TileDesc* tiles, const CUtensorMap* tmapF, long long s, int n_tiles, int ks) {
+  FarTcArgs T{};
+  T.tiles = tiles;
+  T.tmapW = p->d_tmapW;
+  T.tmapF = tmapF;
+  T.far = p->farb;
+  T.status = p->status;
+  T.s = s;
+  T.Lbase = p->Lbase;
+  T.budget = p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL;
+  T.n_tiles = n_tiles;
+  T.ksplit = ks;
+  T.f_kblocks = (int)(p->fsh_ld / 64);
+  return T;
 }
 
 // abm_far_history on a tensor-core plan: one column tile of 96 columns, history
@@ -270,10 +292,8 @@ abm_status far_history_tc(abm_plan p, double alpha, const double* F, long long r
   const int nkb_total = (int)(s / 64);
   const int ks = far_ksplit(1, nkb_total, p->sms, 2);
   CK(cudaMemsetAsync(p->farb, 0, (size_t)2 * 64 * 96 * sizeof(double), st), "far sums reset");
-  FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
-              p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, 1, ks,
-              (int)(p->fsh_ld / 64)};
-  CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, 1, st), "tensor-core far kernel");
+  FarTcArgs T = far_tc_args(p, p->d_tiles, p->d_tmapF, s, 1, ks);
+  CK(launch_far_tc(far_kind(p), T, 1, st), "tensor-core far kernel");
   CK(launch_sum_partials(p->farb, ks, 1, P, C, st), "partial sums");
   CK(cudaStreamSynchronize(st), "synchronize");  // the host-staged tile descriptor must outlive the copy
   return ABM_OK;
@@ -414,11 +434,9 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
         if (ks > 1)  // split tiles add their parts; unsplit tiles store
           CK(cudaMemsetAsync(p->farb, 0, (size_t)n_active * 2 * B * kTrajPerTile * d * sizeof(double), st),
              "far sums reset");
-        FarTcArgs T{p->d_tiles, p->d_tmapW, p->d_tmapF, p->farb, p->status, s, p->Lbase,
-                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, n_active, ks,
-                    (int)(p->fsh_ld / 64)};
+        FarTcArgs T = far_tc_args(p, p->d_tiles, p->d_tmapF, s, n_active, ks);
         Trace tr(p, ABM_KERNEL_FAR, st);
-        CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, n_active, st), "tensor-core far kernel");
+        CK(launch_far_tc(far_kind(p), T, n_active, st), "tensor-core far kernel");
       } else {
         Trace tr(p, ABM_KERNEL_FAR, st);
         CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
@@ -607,7 +625,7 @@ abm_status abm_plan_destroy(abm_plan p) {
   for (auto& w : p->wsets) {
     cudaFree(w.b); cudaFree(w.a); cudaFree(w.c); cudaFree(w.g); cudaFree(w.b32); cudaFree(w.a32); cudaFree(w.Wx);
   }
-  cudaFree(p->Fsh); cudaFree(p->d_tmapW); cudaFree(p->d_tmapF);
+  cudaFree(p->Fsh); cudaFree(p->d_tmapW); cudaFree(p->d_tmapF); 
   cudaFree(p->Xadj); cudaFree(p->Xsh); cudaFree(p->d_tmapX); cudaFree(p->d_atiles);
   cudaFree(p->acc_dp); cudaFree(p->acc_dy0); cudaFree(p->phi0c);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
@@ -978,11 +996,9 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
         if (ks > 1)
           CK(cudaMemsetAsync(p->farb, 0, (size_t)na2 * 2 * B * kTrajPerTile * d * sizeof(double), st),
              "far sums reset");
-        FarTcArgs T{p->d_atiles, p->d_tmapW, p->d_tmapX, p->farb, p->status, s, p->Lbase,
-                    p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL, na2, ks,
-                    (int)(p->fsh_ld / 64)};
+        FarTcArgs T = far_tc_args(p, p->d_atiles, p->d_tmapX, s, na2, ks);
         Trace tr(p, ABM_KERNEL_ADJOINT, st);
-        CK(launch_far_tc(p->o.prec == ABM_PREC_BF16X3_FAR ? 3 : 6, T, na2, st), "adjoint tensor-core far kernel");
+        CK(launch_far_tc(far_kind(p), T, na2, st), "adjoint tensor-core far kernel");
       } else {
         int ks = std::max(1, std::min(16, (2 * p->sms + na2 - 1) / na2));
         while ((size_t)ks * na2 * 2 * B * kTrajPerTile * d > p->farb_cap && ks > 1) --ks;

@@ -24,22 +24,28 @@
 //   F: history pieces, block (t, k / 64) = [96 columns][64 rows], written by
 //      the near kernel at the end of each time tile.
 // Split precision: x = x_hi + x_mid + x_lo, each BF16 (successive residuals).
-//   NPROD = 3: hi*hi + hi*mid + mid*hi      (BF16x3 mode)
-//   NPROD = 6: + hi*lo + mid*mid + lo*hi     (BF16x6 mode, FP32-level error)
+//   kind 3 (BF16x3): hi*hi + hi*mid + mid*hi
+//   kind 6 (BF16x6): + hi*lo + mid*mid + lo*hi (FP32-level error)
 // The leading product hi*hi and the correction products accumulate in
 // separate TMEM accumulators (so the small corrections are not added into a
 // large running sum).  The tensor core's FP32 accumulation of the leading
-// product loses precision with every MMA it adds, so in BF16x6 mode its
-// accumulator holds one 64-row K block only (CB = 1): three buffers rotate,
-// and the epilogue warps add each finished block into a compensated FP32 pair
-// (TwoSum) while the MMAs fill the next (measured on Rossler: pointwise error
-// 9e-7 with 128-256 rows per accumulator, 2e-7 with 64).  BF16x3 drops
-// products of order 2^-16, far above that loss, and keeps CB = 4 blocks (256
-// rows).  The corrections, 2^-8 of the leading term, accumulate in TMEM over
-// the CTA's whole history range and are added once.
+// product loses precision with every MMA it adds, and every switch to a fresh
+// accumulator costs the tensor pipe about 1.3k idle cycles; the K blocks per
+// leading-product accumulator (CB) trade one against the other.  Measured on
+// the Rossler workload (4096 trajectories, BF16x6, pointwise error against the
+// oracle to t = 5 / far-kernel time): CB = 1 2.7e-8 / 195 ms, CB = 2 1.3e-7 /
+// 165 ms, CB = 4 1.8e-6 / 157 ms.  BF16x6 uses CB = 2 (128 rows), three
+// buffers rotating while the epilogue warps add each finished one into a
+// compensated FP32 pair (TwoSum).  BF16x3 drops products of order 2^-16, far
+// above that loss, and keeps CB = 4 (256 rows).  The corrections, 2^-8 of the
+// leading term, accumulate in TMEM over the CTA's whole history range and
+// are added once.
 //
-// Warp roles (320 threads): warp 0 TMA producer, warp 1 TMEM owner + MMA
-// issuer, warps 2..9 epilogue (lane quarter = warp % 4, column half = (warp-2)/4).
+// Warp roles (448 threads): warp 0 TMA producer, warp 1 TMEM owner + MMA
+// issuer, warps 2..13 epilogue (lane quarter = warp % 4, 32-column group =
+// (warp - 2) / 4).  Fourteen warps put at most four on a sub-partition, so a
+// thread may hold 128 registers: the 32 compensated column sums of an
+// epilogue thread (64 registers) fit with room for the TMEM staging.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -51,13 +57,24 @@ namespace abm {
 
 namespace {
 constexpr int KB = 64;          // history rows per K block (128 bytes of BF16)
-constexpr int MAIN_BUFS = 3;    // TMEM buffers of the leading-product accumulator
-constexpr uint32_t CORR_COL = MAIN_BUFS * 128;  // TMEM column of the correction accumulator
 constexpr int NCOL = 96;        // columns per tile (32 trajectories x 3)
 constexpr int A_BYTES = 128 * KB * 2;
 constexpr int B_BYTES = NCOL * KB * 2;
-constexpr int THREADS = 320;
-
+constexpr int EPI_WARPS = 12;   // epilogue warps: 4 lane quarters x 3 column groups
+constexpr int ECOLS = NCOL / 3; // columns per epilogue thread
+constexpr int THREADS = 32 * (2 + EPI_WARPS);
+// Per kind: split products, pieces loaded per operand, ring depths (slots of
+// one K block), K blocks per leading-product accumulator.  Shared memory:
+// BF16x3 3 x 32 KB Toeplitz + 5 x 24 KB history = 216 KB; BF16x6 2 x 48 KB +
+// 3 x 36 KB = 204 KB of the 227 KB a CTA may use.  TMEM (512 columns): three
+// 128-column leading-product buffers and one correction accumulator.
+template <int KIND> struct FarKind;
+template <> struct FarKind<3> {
+  static constexpr int NPROD = 3, NP = 2, WST = 3, FST = 5, CB = 4, NBUF = 3;
+};
+template <> struct FarKind<6> {
+  static constexpr int NPROD = 6, NP = 3, WST = 2, FST = 3, CB = 2, NBUF = 3;
+};
 __device__ __forceinline__ void split3(double x, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
   hi = __double2bfloat16(x);
   double r = x - (double)__bfloat162float(hi);
@@ -65,6 +82,7 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16& hi, __nv_bfloat1
   r -= (double)__bfloat162float(mid);
   lo = __double2bfloat16(r);
 }
+
 }  // namespace
 
 // Pre-expanded Toeplitz weights of one alpha: Wx[p][r][x], p = hi/mid/lo.
@@ -86,16 +104,24 @@ __global__ void build_wx_kernel(const double* __restrict__ b, const double* __re
 }
 
 
-template <int NPROD>
+template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
-  constexpr int NA = NPROD == 3 ? 2 : 3;  // W pieces used
-  constexpr int NB = NA;                  // F pieces used
-  constexpr int STAGES = NPROD == 3 ? 3 : 2;
-  constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
-  constexpr int CB = NPROD == 3 ? 4 : 1;  // K blocks per leading-product accumulator
+  using K = FarKind<KIND>;
+  constexpr int NA = K::NP, NB = K::NP;  // W and F pieces used
+  constexpr int NPROD = K::NPROD;
+  // two load rings: Toeplitz blocks (mostly L2 hits, short latency) and
+  // history blocks (always from HBM), the second one deeper
+  constexpr int WST = K::WST, FST = K::FST;
+  constexpr int W_STAGE = NA * A_BYTES, F_STAGE = NB * B_BYTES;
+  constexpr int CB = K::CB;      // K blocks per leading-product accumulator
+  constexpr int NBUF = K::NBUF;  // leading-product accumulator buffers
+  constexpr uint32_t BUF_STRIDE = 128;
+  constexpr uint32_t CORR_COL = NBUF * BUF_STRIDE;  // the range-wide correction accumulator
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[MAIN_BUFS], acc_empty[MAIN_BUFS], mma_done;
+  uint8_t* smem_f = smem + WST * W_STAGE;
+  __shared__ __align__(8) uint64_t wfull[WST], wempty[WST], ffull[FST], fempty[FST], acc_full[NBUF],
+      acc_empty[NBUF], mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
 
@@ -107,12 +133,14 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
   const int kb_begin = q * per_q;
   const int nkb = max(0, min(nkb_total, kb_begin + per_q) - kb_begin);
   const int nchunks = (nkb + CB - 1) / CB;
+  const int xb0 = (int)((A.Lbase - A.s) / KB);  // Toeplitz block of history block 0
 
   if (tid == 0) abort_flag = 0;
   if (warp == 1) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
-    for (int i = 0; i < STAGES; ++i) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
-    for (int i = 0; i < MAIN_BUFS; ++i) { tc::mbar_init(&acc_full[i], 1); tc::mbar_init(&acc_empty[i], 8); }
+    for (int i = 0; i < WST; ++i) { tc::mbar_init(&wfull[i], 1); tc::mbar_init(&wempty[i], 1); }
+    for (int i = 0; i < FST; ++i) { tc::mbar_init(&ffull[i], 1); tc::mbar_init(&fempty[i], 1); }
+    for (int i = 0; i < NBUF; ++i) { tc::mbar_init(&acc_full[i], 1); tc::mbar_init(&acc_empty[i], EPI_WARPS); }
     tc::mbar_init(&mma_done, 1);
     tc::fence_mbar_init();
   }
@@ -128,24 +156,42 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       for (int p = 0; p < NA; ++p) tc::prefetch_tmap(mW + p);
       for (int p = 0; p < NB; ++p) tc::prefetch_tmap(A.tmapF + p);
       // box coordinates of history block kb: Toeplitz block x = Lbase - s + 64 kb, history block (tile, kb)
-      auto yw = [&](int kb) { return ((int)((A.Lbase - A.s) / KB) + kb) * 128; };
+      auto yw = [&](int kb) { return (xb0 + kb) * 128; };
       auto yf = [&](int kb) { return (tile * A.f_kblocks + kb) * NCOL; };
-      for (int i = 0; i < nkb; ++i) {
-        const int st = i % STAGES;
-        if (i >= STAGES && !tc::mbar_wait(&empty[st], ((i / STAGES) - 1) & 1, A.budget, &abort_flag)) {
-          abort_flag = 1;
-          report_status(A.status, ABM_ERR_TIMEOUT, tile, 1000 + i);
-          // wait (bounded) for the loads already issued before giving up
-          for (int j = max(0, i - STAGES); j < i; ++j)
-            tc::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, A.budget, nullptr);
-          break;
-        }
-        uint8_t* sb = smem + st * STAGE_BYTES;
-        tc::mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-        const int kb = kb_begin + i;
-        for (int p = 0; p < NA; ++p) tc::tma_load_2d(sb + p * A_BYTES, mW + p, &full[st], 0, yw(kb));
+      const uint64_t keep = tc::l2_policy_evict_last(), stream = tc::l2_policy_evict_first();
+      // history block j may load once block j - FST has been consumed, Toeplitz
+      // block i once block i - WST has: history loads run FST - WST blocks
+      // ahead of the Toeplitz loads, issued F(0..lead), then W(i), F(i+lead+1)
+      constexpr int lead = FST - WST;
+      int nf = 0, nw = 0;  // loads issued per ring
+      bool ok = true;
+      auto issue_f = [&]() {
+        const int fs = nf % FST;
+        if (nf >= FST && !tc::mbar_wait(&fempty[fs], ((nf / FST) - 1) & 1, A.budget, &abort_flag)) return false;
+        tc::mbar_arrive_expect_tx(&ffull[fs], F_STAGE);
         for (int p = 0; p < NB; ++p)
-          tc::tma_load_2d(sb + NA * A_BYTES + p * B_BYTES, A.tmapF + p, &full[st], 0, yf(kb));
+          tc::tma_load_2d_hint(smem_f + fs * F_STAGE + p * B_BYTES, A.tmapF + p, &ffull[fs], 0,
+                               yf(kb_begin + nf), stream);
+        ++nf;
+        return true;
+      };
+      for (int j = 0; ok && j <= lead && nf < nkb; ++j) ok = issue_f();
+      for (int i = 0; ok && i < nkb; ++i) {
+        const int ws = i % WST;
+        ok = i < WST || tc::mbar_wait(&wempty[ws], ((i / WST) - 1) & 1, A.budget, &abort_flag);
+        if (!ok) break;
+        tc::mbar_arrive_expect_tx(&wfull[ws], W_STAGE);
+        for (int p = 0; p < NA; ++p)
+          tc::tma_load_2d_hint(smem + ws * W_STAGE + p * A_BYTES, mW + p, &wfull[ws], 0, yw(kb_begin + i), keep);
+        ++nw;
+        if (nf < nkb) ok = issue_f();
+      }
+      if (!ok) {
+        abort_flag = 1;
+        report_status(A.status, ABM_ERR_TIMEOUT, tile, 1000 + nw);
+        // wait (bounded) for the loads already issued before giving up
+        for (int j = max(0, nf - FST); j < nf; ++j) tc::mbar_wait(&ffull[j % FST], (j / FST) & 1, A.budget, nullptr);
+        for (int j = max(0, nw - WST); j < nw; ++j) tc::mbar_wait(&wfull[j % WST], (j / WST) & 1, A.budget, nullptr);
       }
     }
   } else if (warp == 1) {
@@ -155,29 +201,30 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       // (A piece, B piece) of each product: hi=0, mid=1, lo=2
       constexpr int PA[6] = {0, 0, 1, 0, 1, 2};
       constexpr int PB[6] = {0, 1, 0, 2, 1, 0};
-      const uint32_t d_corr = tmem + CORR_COL;
       bool first_corr = true;
       int i = 0;  // K block
       for (int c = 0; c < nchunks && !abort_flag; ++c) {
-        const int buf = c % MAIN_BUFS, use = c / MAIN_BUFS;
+        const int buf = c % NBUF, use = c / NBUF;
         if (use >= 1 && !tc::mbar_wait(&acc_empty[buf], (use - 1) & 1, A.budget, &abort_flag)) {
           abort_flag = 1;
           report_status(A.status, ABM_ERR_TIMEOUT, tile, 2000 + c);
           break;
         }
         tc::fence_after_sync();
-        const uint32_t d_main = tmem + buf * 128;
+        const uint32_t d_main = tmem + buf * BUF_STRIDE;
+        const uint32_t d_corr = tmem + CORR_COL;
         bool first_main = true;
         for (const int iend = min(nkb, (c + 1) * CB); i < iend; ++i) {
-          const int st = i % STAGES;
-          if (!tc::mbar_wait(&full[st], (i / STAGES) & 1, A.budget, &abort_flag)) {
+          const int fs = i % FST, ws = i % WST;
+          if (!tc::mbar_wait(&ffull[fs], (i / FST) & 1, A.budget, &abort_flag) ||
+              !tc::mbar_wait(&wfull[ws], (i / WST) & 1, A.budget, &abort_flag)) {
             abort_flag = 1;
             report_status(A.status, ABM_ERR_TIMEOUT, tile, 3000 + i);
             break;
           }
           tc::fence_after_sync();
-          const uint32_t sa = tc::smem_u32(smem + st * STAGE_BYTES);
-          const uint32_t sbb = sa + NA * A_BYTES;
+          const uint32_t sa = tc::smem_u32(smem + ws * W_STAGE);
+          const uint32_t sbb = tc::smem_u32(smem_f + fs * F_STAGE);
 #pragma unroll
           for (int kk = 0; kk < KB / 16; ++kk) {
 #pragma unroll
@@ -193,7 +240,9 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
               }
             }
           }
-          tc::mma_commit(&empty[st]);  // stage reusable once these MMAs have read it
+          // both slots reusable once these MMAs have read them
+          tc::mma_commit(&fempty[fs]);
+          tc::mma_commit(&wempty[ws]);
         }
         tc::mma_commit(&acc_full[buf]);  // this chunk's leading-product sum is complete
       }
@@ -202,47 +251,49 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       tc::mbar_wait(&mma_done, 0, A.budget, nullptr);
     }
   } else {
-    // ---------------- epilogue: 8 warps ----------------
+    // ---------------- epilogue: 12 warps ----------------
     const int lq = warp & 3;           // TMEM lane quarter this warp may access
-    const int ch = (warp - 2) >> 2;    // column half: 0 -> cols 0..47, 1 -> 48..95
-    const uint32_t lane_base = tmem + ((uint32_t)(lq * 32) << 16) + ch * 48;
-    float hi[48], lo[48];
+    const int cg = (warp - 2) >> 2;    // column group: cols 32 cg .. 32 cg + 31
+    const uint32_t lane_base = tmem + ((uint32_t)(lq * 32) << 16) + cg * ECOLS;
+    constexpr int NG = ECOLS / 16;     // 16-column TMEM loads per accumulator
+    float hi[ECOLS], lo[ECOLS];
 #pragma unroll
-    for (int j = 0; j < 48; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+    for (int j = 0; j < ECOLS; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+    // (hi, lo) += x, compensated (TwoSum)
+    auto two_sum = [&](int jj, float x) {
+      const float s = hi[jj] + x;
+      const float bp = s - hi[jj];
+      lo[jj] += (hi[jj] - (s - bp)) + (x - bp);
+      hi[jj] = s;
+    };
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
-      const int buf = c % MAIN_BUFS;
-      if (!tc::mbar_wait(&acc_full[buf], (c / MAIN_BUFS) & 1, A.budget, &abort_flag)) {
+      const int buf = c % NBUF;
+      if (!tc::mbar_wait(&acc_full[buf], (c / NBUF) & 1, A.budget, &abort_flag)) {
         ok = false;
         break;
       }
       tc::fence_after_sync();
-      uint32_t v[3][16];  // the chunk's leading products: three loads in flight, one wait
+      {
+        uint32_t v[NG][16];  // the chunk's leading products: all loads in flight, one wait each
 #pragma unroll
-      for (int g16 = 0; g16 < 3; ++g16) tc::tmem_ld_32x16_issue(lane_base + buf * 128 + g16 * 16, v[g16]);
+        for (int g16 = 0; g16 < NG; ++g16) tc::tmem_ld_32x16_issue(lane_base + buf * BUF_STRIDE + g16 * 16, v[g16]);
 #pragma unroll
-      for (int g16 = 0; g16 < 3; ++g16) tc::tmem_ld_wait16(v[g16]);
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);  // values are in registers
+        for (int g16 = 0; g16 < NG; ++g16) tc::tmem_ld_wait16(v[g16]);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);  // values are in registers
 #pragma unroll
-      for (int g16 = 0; g16 < 3; ++g16) {
+        for (int g16 = 0; g16 < NG; ++g16)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {  // (hi, lo) += v  (TwoSum)
-          const int jj = g16 * 16 + j;
-          const float x = __uint_as_float(v[g16][j]);
-          const float s = hi[jj] + x;
-          const float bp = s - hi[jj];
-          lo[jj] += (hi[jj] - (s - bp)) + (x - bp);
-          hi[jj] = s;
-        }
+          for (int j = 0; j < 16; ++j) two_sum(g16 * 16 + j, __uint_as_float(v[g16][j]));
       }
     }
     // the correction products, accumulated over the whole range: into lo
     if (ok && nkb > 0 && tc::mbar_wait(&mma_done, 0, A.budget, &abort_flag)) {
       tc::fence_after_sync();
 #pragma unroll
-      for (int g16 = 0; g16 < 3; ++g16) {
+      for (int g16 = 0; g16 < NG; ++g16) {
         float v[16];
         tc::tmem_ld_32x16(lane_base + CORR_COL + g16 * 16, v);
 #pragma unroll
@@ -256,13 +307,13 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       // launch); an unsplit tile stores its sum
       const int r = lq * 32 + lane;    // accumulator row: 0..63 predictor, 64..127 corrector
       const int half = r >> 6, i = r & 63;
-      double* out = A.far + (((size_t)tile * 2 + half) * 64 + i) * NCOL + ch * 48;
+      double* out = A.far + (((size_t)tile * 2 + half) * 64 + i) * NCOL + cg * ECOLS;
       if (A.ksplit == 1) {
 #pragma unroll
-        for (int j = 0; j < 48; ++j) out[j] = (double)hi[j] + (double)lo[j];
+        for (int j = 0; j < ECOLS; ++j) out[j] = (double)hi[j] + (double)lo[j];
       } else {
 #pragma unroll
-        for (int j = 0; j < 48; ++j) atomicAdd(out + j, (double)hi[j] + (double)lo[j]);
+        for (int j = 0; j < ECOLS; ++j) atomicAdd(out + j, (double)hi[j] + (double)lo[j]);
       }
     }
   }
@@ -270,7 +321,6 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
   __syncthreads();
   if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
-
 // Diagnostic path (abm_far_history): split rows [0, s) of a caller's FP64
 // history F (rows x 96) into the BF16 planes of column tile 0 (row 0 zero).
 __global__ void fill_fsh_kernel(const double* __restrict__ F, long long s, __nv_bfloat16* __restrict__ Fsh,
@@ -307,10 +357,12 @@ cudaError_t launch_sum_partials(const double* far, int ksplit, int n_tiles, doub
   return cudaGetLastError();
 }
 
-size_t far_tc_smem_bytes(int nprod) {
-  const int na = nprod == 3 ? 2 : 3, stages = nprod == 3 ? 3 : 2;
-  return (size_t)stages * (na * A_BYTES + na * B_BYTES) + 1024;
+template <int KIND>
+size_t far_tc_smem_bytes_t() {
+  using K = FarKind<KIND>;
+  return (size_t)K::WST * K::NP * A_BYTES + (size_t)K::FST * K::NP * B_BYTES + 1024;
 }
+size_t far_tc_smem_bytes(int kind) { return kind == 3 ? far_tc_smem_bytes_t<3>() : far_tc_smem_bytes_t<6>(); }
 
 cudaError_t launch_build_wx(const double* b, const double* a, long long Mw, long long Lbase, long long Lx,
                             __nv_bfloat16* Wx, cudaStream_t st) {
@@ -319,26 +371,24 @@ cudaError_t launch_build_wx(const double* b, const double* a, long long Mw, long
   return cudaGetLastError();
 }
 
-cudaError_t launch_far_tc(int nprod, const FarTcArgs& A, int n_active, cudaStream_t st) {
-  const size_t smem = far_tc_smem_bytes(nprod);
-  dim3 grid(n_active, A.ksplit);
-  static bool attr3 = false, attr6 = false;  // set once per instantiation
-  if (nprod == 3) {
-    if (!attr3) {
-      cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr3 = true;
-    }
-    far_tc_kernel<3><<<grid, THREADS, smem, st>>>(A);
-  } else {
-    if (!attr6) {
-      cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr6 = true;
-    }
-    far_tc_kernel<6><<<grid, THREADS, smem, st>>>(A);
+template <int KIND>
+cudaError_t launch_far_tc_t(const FarTcArgs& A, int n_active, cudaStream_t st) {
+  const size_t smem = far_tc_smem_bytes_t<KIND>();
+  static bool attr = false;  // set once per instantiation
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(far_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
   }
+  far_tc_kernel<KIND><<<dim3(n_active, A.ksplit), THREADS, smem, st>>>(A);
   return cudaGetLastError();
+}
+
+// kind: 3 = BF16x3, 6 = BF16x6
+cudaError_t launch_far_tc(int kind, const FarTcArgs& A, int n_active, cudaStream_t st) {
+  if (kind == 3) return launch_far_tc_t<3>(A, n_active, st);
+  if (kind == 6) return launch_far_tc_t<6>(A, n_active, st);
+  return cudaErrorInvalidValue;
 }
 
 // Host: 2D tiled tensor map, BF16, 128-byte swizzle, box {64, box_rows}.

@@ -93,20 +93,24 @@ def test_batched_rejects_bad_arguments(abm):
 
 @pytest.mark.parametrize("prec,tol", [("bf16x6", 2e-6), ("bf16x3", 2e-4)])
 @pytest.mark.parametrize("s", [64, 128, 576, 4096, 8192])
-@pytest.mark.parametrize("data", ["normal", "smooth"])
+@pytest.mark.parametrize("data", ["normal", "smooth", "spread"])
 def test_far_history_tensor_cores(abm, prec, tol, s, data):
     """tcgen05 far history (one column tile of 96 columns) against the oracle's
     FP64 history sums over rows [1, s).  Error model of the split: BF16x6 keeps
     every product down to 2^-24 (FP32 level), BF16x3 drops products of order
-    2^-16; the tolerance is relative to sum_k |w_k f_k| per output."""
+    2^-16; the tolerance is relative to sum_k |w_k f_k| per output.  "spread"
+    gives the columns magnitudes from 1e-6 to 1e6 (every piece carries its
+    own exponent, so each column keeps its relative accuracy)."""
     alpha, B = 0.93, 64
     plan = abm.Plan("lorenz", n_max=s + 2 * B, max_batch=32, prec=prec)
     rng = np.random.default_rng(workloads.SEED_INPUTS + s)
     if data == "normal":
         F = rng.standard_normal((s + B + 1, 96))
-    else:  # same-sign, slowly varying columns, like an f history on an attractor lobe
+    elif data == "smooth":  # same-sign, slowly varying columns, like an f history on an attractor lobe
         k = np.arange(s + B + 1)[:, None]
         F = (1.0 + rng.uniform(0, 30, 96))[None, :] * (1.2 + np.sin(k / rng.uniform(20, 400, 96)[None, :]))
+    else:
+        F = rng.standard_normal((s + B + 1, 96)) * 10.0 ** rng.uniform(-6, 6, 96)[None, :]
     P, C = plan.far_history(alpha, torch.as_tensor(F, device="cuda"), s, B, 1, s)
     plan.sync()
     P, C = P.cpu().numpy(), C.cpu().numpy()
@@ -218,7 +222,7 @@ def test_batched_scalar_systems_fp64_and_fp32(abm, system):
 
 
 @pytest.mark.parametrize("near_warps", [1, 2, 3, 5])
-@pytest.mark.parametrize("prec,far_split", [("fp64", 0), ("bf16x6", 1), ("bf16x6", 4)])
+@pytest.mark.parametrize("prec,far_split", [("fp64", 0), ("bf16x6", 1), ("bf16x6", 4), ("bf16x3", 2)])
 def test_batched_launch_shapes(abm, near_warps, prec, far_split):
     """Every near-kernel shape (helper warps per component) and tensor-core
     history split gives the oracle's trajectories: the shapes the autotuner
@@ -228,7 +232,8 @@ def test_batched_launch_shapes(abm, near_warps, prec, far_split):
                     near_warps=near_warps, far_split=far_split)
     Y = plan.solve_batched(batch.alpha, batch.h, batch.N, batch.params, batch.y0).cpu().numpy()
     errs = _errors(batch, Y, t_max=5.0)
-    assert errs.max() <= (1e-11 if prec == "fp64" else 1e-6), (near_warps, prec, far_split, errs.max())
+    tol = {"fp64": 1e-11, "bf16x6": 1e-6, "bf16x3": 1e-4}[prec]
+    assert errs.max() <= tol, (near_warps, prec, far_split, errs.max())
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
