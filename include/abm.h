@@ -111,7 +111,13 @@ typedef struct {
                           may be split across CTAs while the launch takes at most
                           far_split times the waves (CTAs / SM count, rounded up)
                           of the unsplit launch; 0 = 2                           */
-  int reserved[8];     /* must be zero                                            */
+  int near_split;      /* batched near kernel: CTAs per column tile.  A tile's 32
+                          trajectories spread over 2, 4 or 8 CTAs (lanes of a
+                          trajectory sum interleaved slices of the lag window)
+                          so that few active tiles still use many SMs: 0 = the
+                          largest split whose CTAs fit on the SMs, 1 = never,
+                          2, 4 or 8 = that split for every time tile          */
+  int reserved[7];     /* must be zero                                            */
 } abm_plan_opts;
 
 /* Fills *o with the defaults (FP64, n_max = 0, tile_B = 0 ...). */

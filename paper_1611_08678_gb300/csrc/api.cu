@@ -23,7 +23,7 @@ cudaError_t launch_weights_f32(int M, const double* b, const double* a, float* b
 
 cudaError_t launch_batched_setup(int sys, const BatchArgs& A, int n_tiles, cudaStream_t st);
 cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb, int qw,
-                                cudaStream_t st);
+                                int split, cudaStream_t st);
 cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, int n_active, long long s,
                                cudaStream_t st);
 cudaError_t launch_far_tc(int kind, const FarTcArgs& A, int n_active, cudaStream_t st);
@@ -449,7 +449,15 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
       // chain-only form needs fewer instructions
       const int wpc = p->o.near_warps ? p->o.near_warps
                                       : (n_active <= p->sms ? 3 : (n_active <= 2 * p->sms ? 2 : 1));
-      CK(launch_batched_near(p->sys, A, n_active, s, B, wpc, st), "near kernel");
+      // few active tiles: spread each over several CTAs so the FP64 window work
+      // of the tail runs on more SMs
+      int split = p->o.near_split;
+      if (split == 0) {
+        split = 1;
+        for (int c : {8, 4, 2})
+          if ((long long)n_active * c <= p->sms) { split = c; break; }
+      }
+      CK(launch_batched_near(p->sys, A, n_active, s, B, wpc, split, st), "near kernel");
     }
     if (out && j < (int)out->by_tile.size() && !out->by_tile[j].empty()) {
       cudaEvent_t ev = p->hio_ev[j];
@@ -537,6 +545,8 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
   if (o->near_warps != 0 && o->near_warps != 1 && o->near_warps != 2 && o->near_warps != 3 && o->near_warps != 5)
     return ABM_ERR_INVALID_ARG;
   if (o->far_split < 0 || o->far_split > 64) return ABM_ERR_INVALID_ARG;
+  if (o->near_split != 0 && o->near_split != 1 && o->near_split != 2 && o->near_split != 4 && o->near_split != 8)
+    return ABM_ERR_INVALID_ARG;
   const bool tc_prec = o->prec == ABM_PREC_BF16X3_FAR || o->prec == ABM_PREC_BF16X6_FAR;
   if (tc_prec && (sys_dim(sys) != 3 || (o->tile_B && o->tile_B != 64))) return ABM_ERR_UNSUPPORTED;
   abm_plan p = new abm_plan_s();

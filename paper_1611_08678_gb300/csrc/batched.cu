@@ -260,6 +260,159 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
 }
 
 // ---------------------------------------------------------------------------
+// Split near kernel, for time tiles with few active column tiles: column tile
+// t is spread over L CTAs (CTA b: tile b / L, part b % L), each holding
+// T = 32 / L of its trajectories, so that the FP64 window work of a tile
+// runs on L SMs.  One warp per state component; lane = j * L + l serves
+// trajectory j of the part and lag slice l: the window sums of a step run
+// over rows r = l mod L, and the L lanes of a trajectory add their slices
+// with shuffles.  Every lane of a trajectory then runs the same PECE chain
+// (identical values), lane l = 0 stores.  Same inputs, outputs and history
+// layout as batched_near_kernel (the parts of a tile write disjoint columns).
+// ---------------------------------------------------------------------------
+template <int SYS, int L>
+__global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(BatchArgs A, long long s, int nb) {
+  using S = Sys<SYS>;
+  constexpr int D = S::D;
+  constexpr int T = kTrajPerTile / L;       // trajectories of this CTA
+  constexpr int ldt = kTrajPerTile * D;     // columns of the tile history
+  constexpr int ldc = T * D;                // columns of this CTA
+  __shared__ double Fw[65][ldc];            // f rows s..s+64 of this CTA's columns
+  __shared__ double ysh[2][D][T], ysh2[2][D][T];
+  __shared__ double wsb[65], wsa[65];
+  __shared__ double bns[64], cns[64];
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;  // component, lane
+  const int j = lane / L, l = lane % L;                      // trajectory of the part, lag slice
+  const int tile = blockIdx.x / L, part = blockIdx.x % L;
+  const TileDesc& Td = A.tiles[tile];
+  const int tl = part * T + j;               // trajectory lane in the tile
+  const int traj = Td.traj[tl];
+  const int src = traj >= 0 ? traj : Td.traj[0];
+  const double alpha = A.bucket_alpha[Td.bucket];
+  const double* __restrict__ wb = A.bucket_b[Td.bucket];
+  const double* __restrict__ wa = A.bucket_a[Td.bucket];
+  const double* __restrict__ wc = A.bucket_c[Td.bucket];
+  const int col = tl * D + c;                // column in the tile history
+  const int cloc = j * D + c;                // column in this CTA's window
+  double* __restrict__ F = A.F + Td.f_off;
+  constexpr int NT = 32 * D;
+  for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
+  for (int m = threadIdx.x; m < 64; m += NT) { bns[m] = wb[s + m]; cns[m] = wc[s + m]; }
+  for (int m = threadIdx.x; m < ldc; m += NT) Fw[0][m] = F[s * ldt + part * ldc + m];
+  const int kfirst = s > 1 ? 0 : 1;  // window rows relative to s (row 0 is f_0 when s = 0)
+  const double g = A.bucket_g[Td.bucket];
+  const long long Ntraj = traj >= 0 ? (long long)A.N[traj] : 0;
+  const double h = A.h[src];
+  const double hh = traj >= 0 ? A.hhat[traj] : pow(h, alpha);
+  double p[kMaxParams];
+#pragma unroll
+  for (int k = 0; k < S::NP; ++k) p[k] = A.params[(size_t)src * S::NP + k];
+  const double y0c = A.y0[(size_t)src * D + c];
+  float* __restrict__ F32 = A.F32 ? A.F32 + Td.f_off : nullptr;
+  const double F0c = F[col];
+  const double* __restrict__ farP = A.far + (((size_t)tile * 2) * A.B) * ldt + col;
+  const size_t far_q_stride = (size_t)A.n_tiles * 2 * A.B * ldt;
+  const size_t far_c_off = (size_t)A.B * ldt;
+  double nxp = 0.0, nxc = 0.0;  // far sums of the next target, loaded a step ahead
+  if (s > 1 && l == 0) {
+    for (int kq = 0; kq < A.ksplit; ++kq) {
+      nxp += farP[kq * far_q_stride];
+      nxc += farP[kq * far_q_stride + far_c_off];
+    }
+  }
+  bool reported = false;
+  __syncthreads();
+  for (int i = 0; i < nb; ++i) {
+    const long long n = s + i;
+    const int par = i & 1;
+    // lane slice of the window sums over rows [kfirst, i], two chains per sum
+    double sp = 0.0, sc = 0.0, sp1 = 0.0, sc1 = 0.0;
+    int r = kfirst + ((l - kfirst) % L + L) % L;
+    for (; r + L <= i; r += 2 * L) {
+      const double f0 = Fw[r][cloc], f1 = Fw[r + L][cloc];
+      sp = fma(wsb[i - r], f0, sp);
+      sc = fma(wsa[i - r], f0, sc);
+      sp1 = fma(wsb[i - r - L], f1, sp1);
+      sc1 = fma(wsa[i - r - L], f1, sc1);
+    }
+    if (r <= i) {
+      const double f0 = Fw[r][cloc];
+      sp = fma(wsb[i - r], f0, sp);
+      sc = fma(wsa[i - r], f0, sc);
+    }
+    sp += sp1;
+    sc += sc1;
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {  // add the L slices of this trajectory
+      sp += __shfl_xor_sync(0xffffffffu, sp, o);
+      sc += __shfl_xor_sync(0xffffffffu, sc, o);
+    }
+    // far sums and the j = 0 term (lane 0 of the trajectory holds the far sums)
+    sp += __shfl_sync(0xffffffffu, nxp, lane - l);
+    sc += __shfl_sync(0xffffffffu, nxc, lane - l);
+    sp = fma(bns[i], F0c, sp);
+    sc = fma(cns[i], F0c, sc);
+    nxp = nxc = 0.0;
+    if (s > 1 && i + 1 < nb && l == 0) {
+      for (int kq = 0; kq < A.ksplit; ++kq) {
+        nxp += farP[kq * far_q_stride + (size_t)(i + 1) * ldt];
+        nxc += farP[kq * far_q_stride + far_c_off + (size_t)(i + 1) * ldt];
+      }
+    }
+    const double t1 = (double)(n + 1) * h;
+    const double yp = fma(hh, sp, y0c);
+    if (l == 0) ysh[par][c][j] = yp;
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    double ypv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) ypv[k] = ysh[par][k][j];
+    const double fp = S::fc(c, p, alpha, t1, ypv);
+    const double y = fma(hh, fma(g, fp, sc), y0c);
+    if (l == 0) ysh2[par][c][j] = y;
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    double yv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) yv[k] = ysh2[par][k][j];
+    const double fy = S::fc(c, p, alpha, t1, yv);
+    if (l == 0) {
+      Fw[i + 1][cloc] = fy;
+      F[(n + 1) * ldt + col] = fy;
+      if (F32) F32[(n + 1) * ldt + col] = (float)fy;
+      if (n + 1 <= Ntraj) {
+        A.Y[((size_t)traj * A.ldY + (n + 1)) * D + c] = y;
+        if (A.YP) A.YP[((size_t)traj * A.ldY + (n + 1)) * D + c] = yp;
+        if (!reported && !(isfinite(y) && isfinite(fy))) {
+          report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
+          reported = true;
+        }
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+  }
+  if (A.Fsh) {
+    // BF16 split of rows s..s+63 of this CTA's columns (layout as in
+    // batched_near_kernel: K-block tiled, 8 rows of one column and piece per
+    // 16-byte store; row s of the first tile stays zero)
+    constexpr int UNITS = 3 * ldc * 8;
+    for (int u = threadIdx.x; u < UNITS; u += NT) {
+      const int pc = u / (ldc * 8), rem = u % (ldc * 8);
+      const int cc = rem / 8, prt = rem % 8;
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const int row = prt * 8 + rr;
+        __nv_bfloat16 pcs[3];
+        split3_bf16((s == 0 && row == 0) ? 0.0 : Fw[row][cc], pcs);
+        v[rr] = pcs[pc];
+      }
+      __nv_bfloat16* dst = A.Fsh + (size_t)pc * A.fsh_plane +
+                           (((size_t)tile * (A.fsh_ld / 64) + s / 64) * ldt + part * ldc + cc) * 64 + prt * 8;
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Far kernel, FP64 (plain comparator path).  Grid (active tiles, ksplit).
 // 256 threads = 8 warps; warp w owns target rows [w*B/8, (w+1)*B/8), lane =
 // trajectory.  Every lane of a warp uses the same Toeplitz lag, so the weight
@@ -401,10 +554,29 @@ cudaError_t launch_near_t(const BatchArgs& A, int n_active, long long s, int nb,
   return cudaGetLastError();
 }
 
-// wpc: warps per state component, 1 (chain only), 2, 3 or 5 (chain + helpers)
+template <int SYS, int L>
+cudaError_t launch_near_split_t(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+  batched_near_split_kernel<SYS, L><<<n_active * L, 32 * Sys<SYS>::D, 0, st>>>(A, s, nb);
+  return cudaGetLastError();
+}
+
+// wpc: warps per state component, 1 (chain only), 2, 3 or 5 (chain + helpers);
+// split > 1: the split kernel with each column tile spread over split CTAs
 cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long long s, int nb, int wpc,
-                                cudaStream_t st) {
+                                int split, cudaStream_t st) {
   cudaError_t err = cudaErrorInvalidValue;
+  if (split == 2) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_near_split_t<SYS, 2>(A, n_active, s, nb, st)));
+    return err;
+  }
+  if (split == 4) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_near_split_t<SYS, 4>(A, n_active, s, nb, st)));
+    return err;
+  }
+  if (split == 8) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_near_split_t<SYS, 8>(A, n_active, s, nb, st)));
+    return err;
+  }
   if (wpc == 5) {
     ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 4>(A, n_active, s, nb, st)));
   } else if (wpc == 3) {
