@@ -58,10 +58,14 @@ NCU_TRAFFIC = {
 }
 # Batched far kernel: DRAM bytes (read + write) of one captured launch over the
 # algorithmic operand bytes of that launch, per workload and precision, from
-# an ncu capture of the current kernel; the bench line scales it to its own
-# average launch, since DRAM bytes grow with the operand bytes.  Empty until
-# the far kernel as it stands has been captured.
-NCU_TRAFFIC_RATIO = {}
+# an ncu capture of the current kernel (profiles/far_tc_kernel_rossler_batched.md,
+# profiles/far_tc_kernel_financial_batched.md: 512-trajectory cases); the bench
+# line scales it to its own average launch, since DRAM bytes grow with the
+# operand bytes.
+NCU_TRAFFIC_RATIO = {
+    "rossler_batched_bf16x6": (414420224 + 3102464) / 413564928,
+    "financial_batched_bf16x6": (577345024 + 3204864) / 575717376,
+}
 
 
 def parse_args(argv=None):

@@ -115,8 +115,9 @@ typedef struct {
                           trajectories spread over 2, 4 or 8 CTAs (lanes of a
                           trajectory sum interleaved slices of the lag window)
                           so that few active tiles still use many SMs: 0 = the
-                          largest split whose CTAs fit on the SMs, 1 = never,
-                          2, 4 or 8 = that split for every time tile          */
+                          largest of 8 and 4 whose CTAs fit on the SMs, else
+                          none; 1 = never; 2, 4 or 8 = that split for every
+                          time tile                                          */
   int reserved[7];     /* must be zero                                            */
 } abm_plan_opts;
 

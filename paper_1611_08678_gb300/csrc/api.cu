@@ -450,11 +450,13 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
       const int wpc = p->o.near_warps ? p->o.near_warps
                                       : (n_active <= p->sms ? 3 : (n_active <= 2 * p->sms ? 2 : 1));
       // few active tiles: spread each over several CTAs so the FP64 window work
-      // of the tail runs on more SMs
+      // of the tail runs on more SMs.  Measured per step on GB300 (Rossler):
+      // one CTA with helper warps 3.05 us, split 2 3.65 us, split 4 2.7 us,
+      // split 8 2.35 us, so the automatic choice uses 4 or 8 only.
       int split = p->o.near_split;
       if (split == 0) {
         split = 1;
-        for (int c : {8, 4, 2})
+        for (int c : {8, 4})
           if ((long long)n_active * c <= p->sms) { split = c; break; }
       }
       CK(launch_batched_near(p->sys, A, n_active, s, B, wpc, split, st), "near kernel");
