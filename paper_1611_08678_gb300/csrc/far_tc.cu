@@ -256,15 +256,18 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
     const int cg = (warp - 2) >> 2;    // column group: cols 32 cg .. 32 cg + 31
     const uint32_t lane_base = tmem + ((uint32_t)(lq * 32) << 16) + cg * ECOLS;
     constexpr int NG = ECOLS / 16;     // 16-column TMEM loads per accumulator
-    float hi[ECOLS], lo[ECOLS];
+    // compensated FP32 column sums (hi, lo), two columns per 64-bit register
+    // so that the TwoSum runs on packed f32x2 arithmetic (half the instructions)
+    uint64_t hi[ECOLS / 2], lo[ECOLS / 2];
 #pragma unroll
-    for (int j = 0; j < ECOLS; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
-    // (hi, lo) += x, compensated (TwoSum)
-    auto two_sum = [&](int jj, float x) {
-      const float s = hi[jj] + x;
-      const float bp = s - hi[jj];
-      lo[jj] += (hi[jj] - (s - bp)) + (x - bp);
-      hi[jj] = s;
+    for (int j = 0; j < ECOLS / 2; ++j) { hi[j] = 0ull; lo[j] = 0ull; }
+    // (hi, lo) += x for the column pair jp, compensated (TwoSum, elementwise)
+    auto two_sum2 = [&](int jp, uint64_t x) {
+      const uint64_t s = tc::add_f32x2(hi[jp], x);
+      const uint64_t bp = tc::sub_f32x2(s, hi[jp]);
+      const uint64_t e = tc::add_f32x2(tc::sub_f32x2(hi[jp], tc::sub_f32x2(s, bp)), tc::sub_f32x2(x, bp));
+      lo[jp] = tc::add_f32x2(lo[jp], e);
+      hi[jp] = s;
     };
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
@@ -286,7 +289,8 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
 #pragma unroll
         for (int g16 = 0; g16 < NG; ++g16)
 #pragma unroll
-          for (int j = 0; j < 16; ++j) two_sum(g16 * 16 + j, __uint_as_float(v[g16][j]));
+          for (int j = 0; j < 8; ++j)
+            two_sum2(g16 * 8 + j, (uint64_t)v[g16][2 * j] | ((uint64_t)v[g16][2 * j + 1] << 32));
       }
     }
     // the correction products, accumulated over the whole range: into lo
@@ -294,10 +298,12 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       tc::fence_after_sync();
 #pragma unroll
       for (int g16 = 0; g16 < NG; ++g16) {
-        float v[16];
-        tc::tmem_ld_32x16(lane_base + CORR_COL + g16 * 16, v);
+        uint32_t v[16];
+        tc::tmem_ld_32x16_issue(lane_base + CORR_COL + g16 * 16, v);
+        tc::tmem_ld_wait16(v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) lo[g16 * 16 + j] += v[j];
+        for (int j = 0; j < 8; ++j)
+          lo[g16 * 8 + j] = tc::add_f32x2(lo[g16 * 8 + j], (uint64_t)v[2 * j] | ((uint64_t)v[2 * j + 1] << 32));
       }
     } else {
       ok = false;
@@ -308,12 +314,17 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       const int r = lq * 32 + lane;    // accumulator row: 0..63 predictor, 64..127 corrector
       const int half = r >> 6, i = r & 63;
       double* out = A.far + (((size_t)tile * 2 + half) * 64 + i) * NCOL + cg * ECOLS;
+      auto col = [&](int j) {  // column j's sum: hi + lo of its half of the pair
+        const int sh = (j & 1) * 32;
+        return (double)__uint_as_float((uint32_t)(hi[j >> 1] >> sh)) +
+               (double)__uint_as_float((uint32_t)(lo[j >> 1] >> sh));
+      };
       if (A.ksplit == 1) {
 #pragma unroll
-        for (int j = 0; j < ECOLS; ++j) out[j] = (double)hi[j] + (double)lo[j];
+        for (int j = 0; j < ECOLS; ++j) out[j] = col(j);
       } else {
 #pragma unroll
-        for (int j = 0; j < ECOLS; ++j) atomicAdd(out + j, (double)hi[j] + (double)lo[j]);
+        for (int j = 0; j < ECOLS; ++j) atomicAdd(out + j, col(j));
       }
     }
   }
