@@ -75,8 +75,9 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="chen_single",
-                    choices=["chen_single", "lorenz_single", "rossler_batched", "financial_batched",
-                             "lorenz_adjoint"])
+                    choices=["chen_single", "lorenz_single", "hindmarsh_rose_single", "rossler_batched",
+                             "financial_batched", "lorenz_adjoint"])
+    ap.add_argument("--n", type=int, default=0, help="single-trajectory workloads: number of steps N")
     ap.add_argument("--prec", default=None, help="far-history precision of batched workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mib", type=int, default=256)
@@ -87,12 +88,21 @@ def parse_args(argv=None):
 
 
 # ---------------------------------------------------------------------------
-def workload(name):
+# Paper, Table 2: average CUDA run time (s) of the 3-D Hindmarsh-Rose model per
+# number of steps N (unnamed GPU, parameters and precision not stated): context
+# beside the Hindmarsh-Rose bench line, not a target.
+PAPER_TABLE2_CUDA_S = {100000: 169.06, 500000: 1276.42, 1000000: 2670.56, 1500000: 4450.09,
+                       2000000: 6639.45, 2500000: 9229.66, 3000000: 12226.39}
+
+
+def workload(name, n=0):
     from paper_1611_08678_gb300 import workloads as wl
     if name == "chen_single":
-        return wl.chen_single(), "fp64"
+        return (wl.chen_single(n) if n else wl.chen_single()), "fp64"
     if name == "lorenz_single":
-        return wl.lorenz_single(), "fp64"
+        return (wl.lorenz_single(n) if n else wl.lorenz_single()), "fp64"
+    if name == "hindmarsh_rose_single":
+        return (wl.hindmarsh_rose_single(n) if n else wl.hindmarsh_rose_single()), "fp64"
     if name == "rossler_batched":
         return wl.rossler_batched(), "bf16x6"
     if name == "financial_batched":
@@ -285,6 +295,10 @@ def bench_single(args, name, w, world, rank, local):
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    if w.system == "hindmarsh_rose" and N in PAPER_TABLE2_CUDA_S:
+        out["paper_context"] = {"table2_cuda_seconds": PAPER_TABLE2_CUDA_S[N],
+                                "this_run_seconds": total_max / args.steps,
+                                "note": "paper's unnamed GPU, precision and parameters unstated: context only"}
     if rank == 0 and not args.no_cpu_baseline:
         n_sample = min(N, 1 << 15)
         cb, Yo = single_cpu_baseline(w, n_sample)
@@ -683,7 +697,7 @@ def bench_reference(args, name, w, world, rank):
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
-    w, default_prec = workload(args.workload)
+    w, default_prec = workload(args.workload, args.n)
     prec = args.prec or default_prec
     if args.trajectories and not is_single(args.workload) and args.workload != "lorenz_adjoint":
         import numpy as np

@@ -57,14 +57,18 @@ typedef enum {
  *  LORENZ       d=3  (sigma, rho, beta)  x'=sigma(y-x), y'=x(rho-z)-y, z'=xy-beta z
  *  CHEN         d=3  (a, b, c)           x'=a(y-x), y'=(c-a)x-xz+cy, z'=xy-bz
  *  ROSSLER      d=3  (a, b, c)           x'=-y-z, y'=x+ay, z'=b+z(x-c)
- *  FINANCIAL    d=3  (a, b, c)           x'=z+(y-a)x, y'=1-by-x^2, z'=-x-cz     */
+ *  FINANCIAL    d=3  (a, b, c)           x'=z+(y-a)x, y'=1-by-x^2, z'=-x-cz
+ *  HINDMARSH_ROSE d=3 (a, b, c, d, r, s, xR, I)   the 3-D neuron model the paper
+ *                    simulates (Sec. 4, CUDA simulations; Hindmarsh and Rose 1984):
+ *                    x'=y-ax^3+bx^2-z+I, y'=c-dx^2-y, z'=r(s(x-xR)-z)          */
 typedef enum {
   ABM_SYS_LINEAR = 0,
   ABM_SYS_MANUFACTURED = 1,
   ABM_SYS_LORENZ = 2,
   ABM_SYS_CHEN = 3,
   ABM_SYS_ROSSLER = 4,
-  ABM_SYS_FINANCIAL = 5
+  ABM_SYS_FINANCIAL = 5,
+  ABM_SYS_HINDMARSH_ROSE = 6
 } abm_system;
 
 /* Arithmetic of the far-history part (lags older than the current time tile).

@@ -35,7 +35,8 @@ _LIB_PATH = os.path.join(_HERE, "libabm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SYSTEMS = {"linear": 0, "manufactured": 1, "lorenz": 2, "chen": 3, "rossler": 4, "financial": 5}
+SYSTEMS = {"linear": 0, "manufactured": 1, "lorenz": 2, "chen": 3, "rossler": 4, "financial": 5,
+           "hindmarsh_rose": 6}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 

@@ -52,12 +52,12 @@ _Static_assert(LDBL_MANT_DIG == 113, "oracle needs IEEE binary128 long double on
 /* ---- system catalogue (right-hand sides f, Jacobians, parameter derivatives) ----
  * Ids are local to the oracle; the Python wrapper maps system names to them. */
 enum { OR_LINEAR = 0, OR_MANUFACTURED = 1, OR_LORENZ = 2, OR_CHEN = 3,
-       OR_ROSSLER = 4, OR_FINANCIAL = 5, OR_NSYS = 6 };
+       OR_ROSSLER = 4, OR_FINANCIAL = 5, OR_HINDMARSH_ROSE = 6, OR_NSYS = 7 };
 
 int oracle_dim(int sys) {
   switch (sys) {
     case OR_LINEAR: case OR_MANUFACTURED: return 1;
-    case OR_LORENZ: case OR_CHEN: case OR_ROSSLER: case OR_FINANCIAL: return 3;
+    case OR_LORENZ: case OR_CHEN: case OR_ROSSLER: case OR_FINANCIAL: case OR_HINDMARSH_ROSE: return 3;
   }
   return -1;
 }
@@ -67,6 +67,7 @@ int oracle_nparams(int sys) {
     case OR_LINEAR: return 3;
     case OR_MANUFACTURED: return 9;
     case OR_LORENZ: case OR_CHEN: case OR_ROSSLER: case OR_FINANCIAL: return 3;
+    case OR_HINDMARSH_ROSE: return 8;
   }
   return -1;
 }
@@ -84,7 +85,9 @@ static double manu_curve(double alpha, const double* p, double t) {
  *  lorenz       : (sigma, rho, beta)
  *  chen         : (a, b, c)   x'=a(y-x), y'=(c-a)x-xz+cy, z'=xy-bz
  *  rossler      : (a, b, c)   x'=-y-z, y'=x+a y, z'=b+z(x-c)
- *  financial    : (a, b, c)   x'=z+(y-a)x, y'=1-b y-x^2, z'=-x-c z          */
+ *  financial    : (a, b, c)   x'=z+(y-a)x, y'=1-b y-x^2, z'=-x-c z
+ *  hindmarsh_rose: (a, b, c, d, r, s, xR, I)
+ *                 x'=y-a x^3+b x^2-z+I, y'=c-d x^2-y, z'=r(s(x-xR)-z)        */
 void oracle_rhs(int sys, double alpha, const double* p, double t, const double* y, double* f) {
   switch (sys) {
     case OR_LINEAR:
@@ -114,6 +117,11 @@ void oracle_rhs(int sys, double alpha, const double* p, double t, const double* 
       f[0] = y[2] + (y[1] - p[0]) * y[0];
       f[1] = 1.0 - p[1] * y[1] - y[0] * y[0];
       f[2] = -y[0] - p[2] * y[2];
+      break;
+    case OR_HINDMARSH_ROSE:
+      f[0] = y[1] - p[0] * y[0] * y[0] * y[0] + p[1] * y[0] * y[0] - y[2] + p[7];
+      f[1] = p[2] - p[3] * y[0] * y[0] - y[1];
+      f[2] = p[4] * (p[5] * (y[0] - p[6]) - y[2]);
       break;
   }
 }
@@ -166,6 +174,19 @@ void oracle_jac(int sys, double alpha, const double* p, double t, const double* 
       Q[3] = 0.0;    Q[4] = -y[1];  Q[5] = 0.0;
       Q[6] = 0.0;    Q[7] = 0.0;    Q[8] = -y[2];
       break;
+    case OR_HINDMARSH_ROSE: {
+      double x = y[0];
+      J[0] = -3.0 * p[0] * x * x + 2.0 * p[1] * x;  J[1] = 1.0;   J[2] = -1.0;
+      J[3] = -2.0 * p[3] * x;                       J[4] = -1.0;  J[5] = 0.0;
+      J[6] = p[4] * p[5];                           J[7] = 0.0;   J[8] = -p[4];
+      for (int k = 0; k < 24; ++k) Q[k] = 0.0;
+      Q[0] = -x * x * x;  Q[1] = x * x;  Q[7] = 1.0;            /* row 0: a, b, I */
+      Q[8 + 2] = 1.0;     Q[8 + 3] = -x * x;                    /* row 1: c, d */
+      Q[16 + 4] = p[5] * (x - p[6]) - y[2];                     /* row 2: r, s, xR */
+      Q[16 + 5] = p[4] * (x - p[6]);
+      Q[16 + 6] = -p[4] * p[5];
+      break;
+    }
   }
 }
 

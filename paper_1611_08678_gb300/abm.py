@@ -15,7 +15,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libabm_gb300.so")
 
-SYSTEMS = {"linear": 0, "manufactured": 1, "lorenz": 2, "chen": 3, "rossler": 4, "financial": 5}
+SYSTEMS = {"linear": 0, "manufactured": 1, "lorenz": 2, "chen": 3, "rossler": 4, "financial": 5,
+           "hindmarsh_rose": 6}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
 STATUS = {0: "ABM_OK", 1: "ABM_ERR_INVALID_ARG", 2: "ABM_ERR_CUDA", 3: "ABM_ERR_OOM",
           4: "ABM_ERR_TIMEOUT", 5: "ABM_ERR_NONFINITE", 6: "ABM_ERR_UNSUPPORTED"}

@@ -144,6 +144,7 @@ int sys_dim(abm_system s) {
   switch (s) {
     case ABM_SYS_LINEAR: case ABM_SYS_MANUFACTURED: return 1;
     case ABM_SYS_LORENZ: case ABM_SYS_CHEN: case ABM_SYS_ROSSLER: case ABM_SYS_FINANCIAL: return 3;
+    case ABM_SYS_HINDMARSH_ROSE: return 3;
   }
   return -1;
 }
@@ -153,6 +154,7 @@ int sys_nparams(abm_system s) {
     case ABM_SYS_LINEAR: return 3;
     case ABM_SYS_MANUFACTURED: return 9;
     case ABM_SYS_LORENZ: case ABM_SYS_CHEN: case ABM_SYS_ROSSLER: case ABM_SYS_FINANCIAL: return 3;
+    case ABM_SYS_HINDMARSH_ROSE: return 8;
   }
   return -1;
 }

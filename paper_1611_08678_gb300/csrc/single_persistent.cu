@@ -395,6 +395,7 @@ extern "C" abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, 
     case ABM_SYS_LINEAR: d = 1; np = 3; break;
     case ABM_SYS_MANUFACTURED: d = 1; np = 9; break;
     case ABM_SYS_LORENZ: case ABM_SYS_CHEN: case ABM_SYS_ROSSLER: case ABM_SYS_FINANCIAL: d = 3; np = 3; break;
+    case ABM_SYS_HINDMARSH_ROSE: d = 3; np = 8; break;
   }
   if (d < 0) { set_msg(errbuf, errbuf_len, "abm_solve_noalloc: unknown system"); return ABM_ERR_INVALID_ARG; }
   if (N < 1 || N > kNoallocMaxN) {

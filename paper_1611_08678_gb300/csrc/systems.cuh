@@ -161,6 +161,39 @@ struct Sys<ABM_SYS_FINANCIAL> {
   }
 };
 
+// The 3-D Hindmarsh-Rose neuron model (the system the paper simulates in
+// Sec. 4, CUDA simulations), parameters (a, b, c, d, r, s, xR, I).
+template <>
+struct Sys<ABM_SYS_HINDMARSH_ROSE> {
+  static constexpr int D = 3, NP = 8;
+  // component c of f (the same arithmetic as f, one component)
+  __device__ __forceinline__ static double fc(int c, const double* p, double, double, const double* y) {
+    if (c == 0) return fma(fma(-p[0], y[0], p[1]), y[0] * y[0], y[1] - y[2] + p[7]);
+    if (c == 1) return fma(-p[3], y[0] * y[0], p[2] - y[1]);
+    return p[4] * fma(p[5], y[0] - p[6], -y[2]);
+  }
+  __device__ __forceinline__ static void f(const double* p, double, double, const double* y,
+                                           double* out) {
+    out[0] = fma(fma(-p[0], y[0], p[1]), y[0] * y[0], y[1] - y[2] + p[7]);
+    out[1] = fma(-p[3], y[0] * y[0], p[2] - y[1]);
+    out[2] = p[4] * fma(p[5], y[0] - p[6], -y[2]);
+  }
+  __device__ __forceinline__ static void jac(const double* p, double, double, const double* y,
+                                             double* J, double* Q) {
+    const double x = y[0];
+    J[0] = x * fma(-3.0 * p[0], x, 2.0 * p[1]);  J[1] = 1.0;   J[2] = -1.0;
+    J[3] = -2.0 * p[3] * x;                     J[4] = -1.0;  J[5] = 0.0;
+    J[6] = p[4] * p[5];                         J[7] = 0.0;   J[8] = -p[4];
+#pragma unroll
+    for (int k = 0; k < 3 * NP; ++k) Q[k] = 0.0;
+    Q[0] = -x * x * x;  Q[1] = x * x;  Q[7] = 1.0;      // row 0: a, b, I
+    Q[NP + 2] = 1.0;    Q[NP + 3] = -x * x;             // row 1: c, d
+    Q[2 * NP + 4] = fma(p[5], x - p[6], -y[2]);         // row 2: r, s, xR
+    Q[2 * NP + 5] = p[4] * (x - p[6]);
+    Q[2 * NP + 6] = -p[4] * p[5];
+  }
+};
+
 // Runtime system id -> template instantiation.
 #define ABM_DISPATCH_SYSTEM(sys, BODY)                                   \
   switch (sys) {                                                         \
@@ -170,6 +203,7 @@ struct Sys<ABM_SYS_FINANCIAL> {
     case ABM_SYS_CHEN: { constexpr int SYS = ABM_SYS_CHEN; BODY; } break;                 \
     case ABM_SYS_ROSSLER: { constexpr int SYS = ABM_SYS_ROSSLER; BODY; } break;           \
     case ABM_SYS_FINANCIAL: { constexpr int SYS = ABM_SYS_FINANCIAL; BODY; } break;       \
+    case ABM_SYS_HINDMARSH_ROSE: { constexpr int SYS = ABM_SYS_HINDMARSH_ROSE; BODY; } break; \
     default: break;                                                      \
   }
 

@@ -30,8 +30,15 @@ import numpy as np
 SEED_INPUTS = 1611
 SEED_PERTURB = 8678
 
-DIMS = {"linear": 1, "manufactured": 1, "lorenz": 3, "chen": 3, "rossler": 3, "financial": 3}
-NPARAMS = {"linear": 3, "manufactured": 9, "lorenz": 3, "chen": 3, "rossler": 3, "financial": 3}
+DIMS = {"linear": 1, "manufactured": 1, "lorenz": 3, "chen": 3, "rossler": 3, "financial": 3,
+        "hindmarsh_rose": 3}
+NPARAMS = {"linear": 3, "manufactured": 9, "lorenz": 3, "chen": 3, "rossler": 3, "financial": 3,
+           "hindmarsh_rose": 8}
+
+# The 3-D Hindmarsh-Rose model in its chaotic-bursting regime: (a, b, c, d, r,
+# s, xR, I).  The paper simulates this model (Sec. 4) without stating its
+# parameters, alpha, h or y0; these are this project's choices.
+HR_PARAMS = [1.0, 3.0, 1.0, 5.0, 0.006, 4.0, -1.6, 3.25]
 
 
 @dataclass
@@ -76,6 +83,11 @@ def lorenz_single(N: int = 8192) -> Batch:
 
 def chen_single(N: int = 1 << 18) -> Batch:
     return _single("chen", 0.9, 0.001, N, [35.0, 3.0, 28.0], [-9.0, -5.0, 14.0], "chen_single")
+
+
+def hindmarsh_rose_single(N: int = 100000) -> Batch:
+    """The paper's workload at its own sizes (N = 1e5 .. 3e6 in Table 2)."""
+    return _single("hindmarsh_rose", 0.98, 0.01, N, HR_PARAMS, [0.1, 0.2, 0.3], "hindmarsh_rose_single")
 
 
 def rossler_batched(M: int = 4096, n_lo: int = 1 << 12, n_hi: int = 1 << 16, n_alpha: int = 8,
@@ -135,6 +147,10 @@ def random_batch(system: str, M: int, n_lo: int, n_hi: int, alphas, h: float = 0
     elif system == "chen":
         params = np.tile(np.array([35.0, 3.0, 28.0]), (M, 1))
         y0 = np.array([-9.0, -5.0, 14.0]) + rng.normal(0.0, 0.1, (M, 3))
+    elif system == "hindmarsh_rose":
+        params = np.tile(np.array(HR_PARAMS), (M, 1))
+        params[:, 7] = rng.uniform(2.9, 3.3, M)  # the input current I
+        y0 = rng.uniform(-1, 1, (M, 3))
     elif system == "linear":
         params = np.stack([rng.uniform(-2, 0.5, M), rng.uniform(-1, 1, M), rng.uniform(-1, 1, M)], axis=1)
         y0 = rng.uniform(-1, 1, (M, 1))

@@ -49,6 +49,7 @@ def _rel(a, b):
     ("lorenz", 5, 40, 300, [0.9, 0.98]),
     ("financial", 40, 60, 200, [0.95]),
     ("rossler", 36, 100, 260, [0.85, 1.0]),
+    ("hindmarsh_rose", 20, 60, 200, [0.95]),
 ])
 def test_adjoint_fp64_matches_tangent_linear_oracle(abm, system, M, n_lo, n_hi, alphas):
     batch, plan, Y, YP, target, G, dp, dy0 = _case(abm, system, M, n_lo, n_hi, alphas, "fp64")

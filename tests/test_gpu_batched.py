@@ -44,6 +44,7 @@ def _errors(batch, Y, t_max=None, YP=None):
     ("lorenz", [0.9, 0.98], 100, 1300, 45),
     ("rossler", list(np.linspace(0.85, 1.0, 8)), 64, 1100, 80),
     ("financial", [0.95], 500, 900, 33),
+    ("hindmarsh_rose", [0.9, 0.98], 100, 900, 40),
 ])
 def test_batched_fp64_matches_oracle(abm, system, alphas, n_lo, n_hi, M):
     batch = workloads.random_batch(system, M, n_lo, n_hi, alphas)

@@ -89,6 +89,8 @@ CASES = [
     ("rossler", 0.9, 0.005, 2000, [0.2, 0.2, 5.7], [0.5, -0.3, 0.1]),
     ("financial", 0.95, 0.01, 1500, [3.0, 0.1, 1.0], [2.0, 3.0, 2.0]),
     ("lorenz", 1.0, 0.01, 300, [10.0, 28.0, 8.0 / 3.0], [0.1, 0.1, 0.1]),
+    ("hindmarsh_rose", 0.98, 0.01, 2500, workloads.HR_PARAMS, [0.1, 0.2, 0.3]),
+    ("hindmarsh_rose", 0.8, 0.02, 700, workloads.HR_PARAMS, [-1.2, -5.0, 1.0]),
 ]
 
 

@@ -228,6 +228,12 @@ def test_alpha_one_order_two_to_exponential():
 # Right-hand sides of the workload systems: equilibria, Jacobian consistency,
 # and the Lorenz flow's constant divergence -(sigma + 1 + beta).
 # ---------------------------------------------------------------------------
+# The 3-D Hindmarsh-Rose model's chaotic-bursting parameters (a, b, c, d, r, s,
+# xR, I) from Hindmarsh and Rose (1984); the paper simulates this model without
+# stating its parameters.
+HR_PARAMS = [1.0, 3.0, 1.0, 5.0, 0.006, 4.0, -1.6, 3.25]
+
+
 def _equilibria():
     s, r, bt = 10.0, 28.0, 8.0 / 3.0
     q = math.sqrt(bt * (r - 1))
@@ -237,11 +243,16 @@ def _equilibria():
     ys = [(-rc + sg * math.sqrt(rc * rc - 4 * ra * rb)) / (2 * ra) for sg in (1, -1)]
     fa, fb, fc = 3.0, 0.1, 1.0
     xf = math.sqrt(1 - fb * (fa + 1 / fc))
+    # Hindmarsh-Rose: y = c - d x^2 and z = s (x - xR) reduce f = 0 to the cubic
+    # a x^3 + (d - b) x^2 + s x - (c + s xR + I) = 0, solved by numpy.roots
+    ha, hb, hc, hd, hr, hs, hx, hI = HR_PARAMS
+    hroots = [z.real for z in np.roots([ha, hd - hb, hs, -(hc + hs * hx + hI)]) if abs(z.imag) < 1e-9]
     return [
         ("lorenz", [s, r, bt], [[0, 0, 0], [q, q, r - 1], [-q, -q, r - 1]]),
         ("chen", [ca, cb, cc], [[0, 0, 0], [w, w, 2 * cc - ca], [-w, -w, 2 * cc - ca]]),
         ("rossler", [ra, rb, rc], [[-ra * y, y, -y] for y in ys]),
         ("financial", [fa, fb, fc], [[0, 1 / fb, 0], [xf, fa + 1 / fc, -xf / fc], [-xf, fa + 1 / fc, xf / fc]]),
+        ("hindmarsh_rose", HR_PARAMS, [[x, hc - hd * x * x, hs * (x - hx)] for x in hroots]),
     ]
 
 
@@ -254,11 +265,14 @@ def test_rhs_vanishes_at_equilibria(system, p, points):
 
 @pytest.mark.parametrize("system,p", [("lorenz", [10.0, 28.0, 8 / 3]), ("chen", [35.0, 3.0, 28.0]),
                                       ("rossler", [0.2, 0.2, 5.7]), ("financial", [3.0, 0.1, 1.0]),
+                                      ("hindmarsh_rose", None),
                                       ("linear", [-1.2, 0.3, 0.5]), ("manufactured", None)])
 def test_jacobians_match_central_differences(system, p):
     alpha = 0.8
     if system == "manufactured":
         p, _, _ = _manufactured_params(alpha, -1.0, -0.5)
+    if system == "hindmarsh_rose":
+        p = HR_PARAMS
     rng = np.random.default_rng(1611)
     d = oracle.dim(system)
     for _ in range(4):
@@ -316,12 +330,15 @@ def test_history_brute_force_and_solve_identity():
     ("financial", [3.0, 0.1, 1.0], [2.0, 3.0, 2.0], 0.95, 0.01, 80),
     ("rossler", [0.2, 0.2, 5.7], [0.5, -0.3, 0.1], 0.9, 0.01, 80),
     ("chen", [35.0, 3.0, 28.0], [-9.0, -5.0, 14.0], 0.9, 0.001, 60),
+    ("hindmarsh_rose", None, [0.1, 0.2, 0.3], 0.98, 0.01, 60),
     ("manufactured", None, None, 0.6, 0.02, 50),
 ])
 def test_tangent_matches_central_differences(system, p, y0, alpha, h, N):
     if system == "manufactured":
         p, e0, _ = _manufactured_params(alpha, -1.0, -0.5)
         y0 = [e0 + 0.1]
+    if system == "hindmarsh_rose":
+        p = HR_PARAMS
     d = oracle.dim(system)
     rng = np.random.default_rng(8678)
     Y, _ = oracle.solve(system, alpha, h, N, p, y0)
