@@ -299,6 +299,176 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) adjoint_near_kern
   }
 }
 
+// The reverse steps with each forward column tile spread over L CTAs (as the
+// forward split near kernel): CTA b serves tile b / L, trajectories
+// (b % L) * T .. + T - 1 of it (T = 32 / L); one warp per state component,
+// lane = j * L + l serves trajectory j and lag slice l of the two windows,
+// the slices added with shuffles.  All lanes of a trajectory run the same
+// reverse step (identical values); lane l = 0 stores.  Used when few tiles
+// are active, so that the FP64 window work runs on more SMs.
+template <int SYS, int L>
+__global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_near_split_kernel(AdjArgs A, long long s, int nb) {
+  using S = Sys<SYS>;
+  constexpr int D = S::D, NP = S::NP, ld = kTrajPerTile * D;
+  constexpr int T = kTrajPerTile / L, ldc = T * D, NT = 32 * D;
+  __shared__ double Wm[65][ldc], Wl[65][ldc];  // mu~ / lambda~ rows s..s+64 of this CTA's columns
+  __shared__ double wsb[65], wsa[65];
+  __shared__ double xsh[D][T];
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = lane / L, l = lane % L;
+  const int tile = blockIdx.x / L, part = blockIdx.x % L;
+  const int tl = part * T + j, col = tl * D + c, cloc = j * D + c;
+  const TileDesc& Td = A.tiles[tile];
+  const int traj = Td.traj[tl];
+  const int src = traj >= 0 ? traj : Td.traj[0];
+  const double* wb = A.bucket_b[Td.bucket];
+  const double* wa = A.bucket_a[Td.bucket];
+  double* Xm = A.X + A.atiles[2 * tile].f_off;
+  double* Xl = A.X + A.atiles[2 * tile + 1].f_off;
+  for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
+  for (int m = threadIdx.x; m < ldc; m += NT) {
+    Wm[0][m] = Xm[s * ld + part * ldc + m];
+    Wl[0][m] = Xl[s * ld + part * ldc + m];
+  }
+  const double alpha = A.bucket_alpha[Td.bucket];
+  const double* wc = A.bucket_c[Td.bucket];
+  const double g = A.bucket_g[Td.bucket];
+  const long long Ni = traj >= 0 ? (long long)A.N[traj] : -1;
+  const double h = A.h[src];
+  const double hh = traj >= 0 ? A.hhat[traj] : 0.0;
+  double p[kMaxParams];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) p[k] = A.params[(size_t)src * NP + k];
+  double adp[NP], ady0 = 0.0, phc = 0.0;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) adp[k] = 0.0;
+  if (traj >= 0) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) adp[k] = A.acc_dp[((size_t)traj * D + c) * NP + k];
+    ady0 = A.acc_dy0[(size_t)traj * D + c];
+    phc = A.phi0c[(size_t)traj * D + c];
+  }
+  __syncthreads();
+  const size_t fstride = (size_t)A.far_tiles * 2 * A.B * ld;
+  for (int i = 0; i < nb; ++i) {
+    const long long t = s + i;
+    const long long k = Ni - 1 - t;  // forward index of this reverse step
+    const bool act = k >= 0;
+    const long long kk = act ? k : 0;
+    double yk[D], ypk[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      yk[q] = A.Y[((size_t)src * A.ldY + kk) * D + q];
+      ypk[q] = A.YP[((size_t)src * A.ldY + kk) * D + q];
+    }
+    const double Gk = A.G[((size_t)src * A.ldY + kk) * D + c];
+    // lane slice l of the two windows, rows r = l mod L in [0, i]
+    double Sm = 0.0, Sl = 0.0, Sm1 = 0.0, Sl1 = 0.0;
+    int r = l;
+    for (; r + L <= i; r += 2 * L) {
+      Sm = fma(wsb[i - r], Wm[r][cloc], Sm);
+      Sl = fma(wsa[i - r], Wl[r][cloc], Sl);
+      Sm1 = fma(wsb[i - r - L], Wm[r + L][cloc], Sm1);
+      Sl1 = fma(wsa[i - r - L], Wl[r + L][cloc], Sl1);
+    }
+    if (r <= i) {
+      Sm = fma(wsb[i - r], Wm[r][cloc], Sm);
+      Sl = fma(wsa[i - r], Wl[r][cloc], Sl);
+    }
+    Sm += Sm1;
+    Sl += Sl1;
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+      Sm += __shfl_xor_sync(0xffffffffu, Sm, o);
+      Sl += __shfl_xor_sync(0xffffffffu, Sl, o);
+    }
+    if (s > 0) {  // far sums (mu~ rows through b, lambda~ rows through a)
+      for (int kq = 0; kq < A.far_ksplit; ++kq) {
+        Sm += A.far[kq * fstride + ((((size_t)2 * tile) * 2 + 0) * A.B + i) * ld + col];
+        Sl += A.far[kq * fstride + ((((size_t)2 * tile + 1) * 2 + 1) * A.B + i) * ld + col];
+      }
+    }
+    const double phi = hh * (Sm + (k >= 1 ? Sl : phc));
+    if (l == 0) xsh[c][j] = phi;
+    bar_components<D>();
+    double Jy[D * D], Qy[D * NP], Jp[D * D], Qp[D * NP];
+    S::jac(p, alpha, (double)kk * h, yk, Jy, Qy);
+    S::jac(p, alpha, (double)kk * h, ypk, Jp, Qp);
+    double Jyc[D], Jpc[D], Qyc[NP], Qpc[NP];
+#pragma unroll
+    for (int q = 0; q < D; ++q) { Jyc[q] = Jy[q * D]; Jpc[q] = Jp[q * D]; }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) { Qyc[q] = Qy[q]; Qpc[q] = Qp[q]; }
+#pragma unroll
+    for (int cc = 1; cc < D; ++cc) {
+      if (c == cc) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) { Jyc[q] = Jy[q * D + cc]; Jpc[q] = Jp[q * D + cc]; }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) { Qyc[q] = Qy[cc * NP + q]; Qpc[q] = Qp[cc * NP + q]; }
+      }
+    }
+    double lam = Gk;
+#pragma unroll
+    for (int q = 0; q < D; ++q) lam = fma(Jyc[q], xsh[q][j], lam);
+    bar_components<D>();
+    if (l == 0) xsh[c][j] = lam;
+    bar_components<D>();
+    double jl = 0.0;
+#pragma unroll
+    for (int q = 0; q < D; ++q) jl = fma(Jpc[q], xsh[q][j], jl);
+    bar_components<D>();
+    const double mu = hh * g * jl;
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) adp[q] = fma(Qyc[q], phi, adp[q]);
+      if (k >= 1) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) adp[q] = fma(hh * g * Qpc[q], lam, adp[q]);
+        ady0 += lam + mu;
+        phc = fma(wc[k - 1], lam, phc);
+      } else if (l == 0) {  // k = 0: lambda here is G_0 + J_0^T phi_0
+        A.dy0[(size_t)traj * D + c] = ady0 + lam;
+      }
+      if (l == 0 && !(isfinite(lam) && isfinite(phi))) report_status(A.status, ABM_ERR_NONFINITE, traj, k);
+    }
+    const bool row = act && k >= 1;
+    if (l == 0) {
+      Wm[i + 1][cloc] = row ? mu : 0.0;
+      Wl[i + 1][cloc] = row ? lam : 0.0;
+      Xm[(t + 1) * ld + col] = row ? mu : 0.0;
+      Xl[(t + 1) * ld + col] = row ? lam : 0.0;
+    }
+    bar_components<D>();
+  }
+  if (traj >= 0 && l == 0) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) A.acc_dp[((size_t)traj * D + c) * NP + q] = adp[q];
+    A.acc_dy0[(size_t)traj * D + c] = ady0;
+    A.phi0c[(size_t)traj * D + c] = phc;
+  }
+  if (A.Xsh) {
+    // BF16 split of rows s..s+63 of both histories, this CTA's columns
+    constexpr int UNITS = 2 * 3 * ldc * 8;
+    for (int u = threadIdx.x; u < UNITS; u += NT) {
+      const int hist = u / (3 * ldc * 8), rem0 = u % (3 * ldc * 8);
+      const int pc = rem0 / (ldc * 8), rem = rem0 % (ldc * 8);
+      const int cc = rem / 8, prt = rem % 8;
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        __nv_bfloat16 pcs[3];
+        split3_bf16_adj(hist == 0 ? Wm[prt * 8 + rr][cc] : Wl[prt * 8 + rr][cc], pcs);
+        v[rr] = pcs[pc];
+      }
+      __nv_bfloat16* dst = A.Xsh + (size_t)pc * A.xsh_plane +
+                           (((size_t)(2 * tile + hist) * (A.xsh_ld / 64) + s / 64) * ld + part * ldc + cc) * 64 +
+                           prt * 8;
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+    }
+  }
+}
+
 template <int SYS>
 __global__ void adjoint_finish_kernel(AdjArgs A, int M) {
   using S = Sys<SYS>;
@@ -337,10 +507,25 @@ cudaError_t launch_adjoint_near_t(const AdjArgs& A, int n_active, long long s, i
   return cudaGetLastError();
 }
 
-// wpc: warps per state component, 1 (chain only), 2 or 3 (chain + helpers)
+template <int SYS, int L>
+cudaError_t launch_adjoint_near_split_t(const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+  adjoint_near_split_kernel<SYS, L><<<n_active * L, 32 * Sys<SYS>::D, 0, st>>>(A, s, nb);
+  return cudaGetLastError();
+}
+
+// wpc: warps per state component, 1 (chain only), 2 or 3 (chain + helpers);
+// split 4 or 8: the split kernel with each forward tile spread over split CTAs
 cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, int wpc,
-                                cudaStream_t st) {
+                                int split, cudaStream_t st) {
   cudaError_t err = cudaErrorInvalidValue;
+  if (split == 4) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_adjoint_near_split_t<SYS, 4>(A, n_active, s, nb, st)));
+    return err;
+  }
+  if (split == 8) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_adjoint_near_split_t<SYS, 8>(A, n_active, s, nb, st)));
+    return err;
+  }
   if (wpc == 3) {
     ABM_DISPATCH_SYSTEM(sys, err = (launch_adjoint_near_t<SYS, 2>(A, n_active, s, nb, st)));
   } else if (wpc == 2) {

@@ -35,7 +35,7 @@ cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, lo
 cudaError_t launch_sum_partials(const double* far, int ksplit, int n_tiles, double* P, double* C, cudaStream_t st);
 cudaError_t launch_adjoint_setup(int sys, const AdjArgs& A, int n_tiles, cudaStream_t st);
 cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, int wpc,
-                                cudaStream_t st);
+                                int split, cudaStream_t st);
 cudaError_t launch_adjoint_finish(int sys, const AdjArgs& A, int M, cudaStream_t st);
 }  // namespace abm
 
@@ -1027,7 +1027,13 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
     // warps per component as in the forward near kernel (5 is not built here)
     const int wpc = p->o.near_warps ? std::min(p->o.near_warps, 3)
                                     : (n_active <= p->sms ? 3 : (n_active <= 2 * p->sms ? 2 : 1));
-    CK(launch_adjoint_near(p->sys, A, n_active, s, B, wpc, st), "adjoint near kernel");
+    // few active tiles: spread each over 4 or 8 CTAs as in the forward solve
+    // (the adjoint split kernel is built for 4 and 8 only)
+    int split = p->o.near_split == 4 || p->o.near_split == 8 ? p->o.near_split : 1;
+    if (p->o.near_split == 0)
+      for (int c : {8, 4})
+        if ((long long)n_active * c <= p->sms) { split = c; break; }
+    CK(launch_adjoint_near(p->sys, A, n_active, s, B, wpc, split, st), "adjoint near kernel");
   }
   {
     Trace tr(p, ABM_KERNEL_ADJOINT, st);

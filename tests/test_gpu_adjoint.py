@@ -27,9 +27,9 @@ def _loss_partials(batch, Y, target):
     return G
 
 
-def _case(abm, system, M, n_lo, n_hi, alphas, prec, seed=workloads.SEED_PERTURB):
+def _case(abm, system, M, n_lo, n_hi, alphas, prec, seed=workloads.SEED_PERTURB, near_split=0):
     batch = workloads.random_batch(system, M, n_lo, n_hi, alphas)
-    plan = abm.Plan(system, n_max=int(batch.N.max()), max_batch=M, prec=prec)
+    plan = abm.Plan(system, n_max=int(batch.N.max()), max_batch=M, prec=prec, near_split=near_split)
     Y, YP = plan.solve_batched(batch.alpha, batch.h, batch.N, batch.params, batch.y0, want_yp=True)
     Yn = Y.cpu().numpy()
     rng = np.random.default_rng(seed)
@@ -60,6 +60,25 @@ def test_adjoint_fp64_matches_tangent_linear_oracle(abm, system, M, n_lo, n_hi, 
         worst = max(worst, _rel(dp[i], op), _rel(dy0[i], oy))
     print(f"{system} fp64 adjoint vs tangent-linear: max rel {worst:.2e}")
     assert worst <= 1e-9
+
+
+@pytest.mark.parametrize("near_split", [1, 4, 8])
+@pytest.mark.parametrize("system,M,n_lo,n_hi,alphas", [
+    ("lorenz", 40, 60, 300, [0.9, 0.98]),
+    ("hindmarsh_rose", 12, 64, 200, [0.95]),
+])
+def test_adjoint_near_split_matches_tangent_linear_oracle(abm, near_split, system, M, n_lo, n_hi, alphas):
+    """The adjoint near kernel with each forward tile spread over 4 or 8 CTAs
+    (lanes of a trajectory summing interleaved lag slices of both windows)
+    gives the tangent-linear oracle's gradients like the one-CTA kernel."""
+    batch, plan, Y, YP, target, G, dp, dy0 = _case(abm, system, M, n_lo, n_hi, alphas, "fp64",
+                                                   near_split=near_split)
+    worst = 0.0
+    for i in range(batch.M):
+        n = int(batch.N[i])
+        op, oy = oracle.tangent(system, batch.alpha[i], batch.h[i], n, batch.params[i], batch.y0[i], G[i, : n + 1])
+        worst = max(worst, _rel(dp[i], op), _rel(dy0[i], oy))
+    assert worst <= 1e-9, (near_split, system, worst)
 
 
 def test_adjoint_matches_central_differences_of_gpu_solve(abm):
