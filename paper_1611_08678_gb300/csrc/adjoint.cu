@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) adjoint_near_kern
         } else {  // k = 0: lambda here is G_0 + J_0^T phi_0
           A.dy0[(size_t)traj * D + c] = ady0 + lam;
         }
-        if (!(isfinite(lam) && isfinite(phi))) report_status(A.status, ABM_ERR_NONFINITE, traj, k);
+        if (!(finite_bits(lam) && finite_bits(phi))) report_status(A.status, ABM_ERR_NONFINITE, traj, k);
       }
       const bool row = act && k >= 1;
       Wm[i + 1][col] = row ? mu : 0.0;
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_near_split_kernel(Ad
       } else if (l == 0) {  // k = 0: lambda here is G_0 + J_0^T phi_0
         A.dy0[(size_t)traj * D + c] = ady0 + lam;
       }
-      if (l == 0 && !(isfinite(lam) && isfinite(phi))) report_status(A.status, ABM_ERR_NONFINITE, traj, k);
+      if (l == 0 && !(finite_bits(lam) && finite_bits(phi))) report_status(A.status, ABM_ERR_NONFINITE, traj, k);
     }
     const bool row = act && k >= 1;
     if (l == 0) {

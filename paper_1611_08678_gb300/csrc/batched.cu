@@ -135,10 +135,8 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
     // far partial sums of the next target, loaded a step ahead
     double nxp = 0.0, nxc = 0.0;
     if (s > 1) {
-      for (int kq = 0; kq < A.ksplit; ++kq) {
-        nxp += farP[kq * far_q_stride];
-        nxc += farP[kq * far_q_stride + far_c_off];
-      }
+      nxp = sum_parts(farP, A.ksplit, far_q_stride);
+      nxc = sum_parts(farP + far_c_off, A.ksplit, far_q_stride);
     }
     bool reported = false;
     __syncthreads();
@@ -148,10 +146,8 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
       double sp = fma(bns[i], F0c, nxp), sc = fma(cns[i], F0c, nxc);
       nxp = nxc = 0.0;
       if (s > 1 && i + 1 < nb) {
-        for (int kq = 0; kq < A.ksplit; ++kq) {
-          nxp += farP[kq * far_q_stride + (size_t)(i + 1) * ld];
-          nxc += farP[kq * far_q_stride + far_c_off + (size_t)(i + 1) * ld];
-        }
+        nxp = sum_parts(farP + (size_t)(i + 1) * ld, A.ksplit, far_q_stride);
+        nxc = sum_parts(farP + far_c_off + (size_t)(i + 1) * ld, A.ksplit, far_q_stride);
       }
       if constexpr (HS > 0) {
 #pragma unroll
@@ -200,7 +196,7 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
       if (n + 1 <= Ntraj) {
         A.Y[((size_t)traj * A.ldY + (n + 1)) * D + c] = y;
         if (A.YP) A.YP[((size_t)traj * A.ldY + (n + 1)) * D + c] = yp;
-        if (!reported && !(isfinite(y) && isfinite(fy))) {
+        if (!reported && !(finite_bits(y) && finite_bits(fy))) {
           report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
           reported = true;
         }
@@ -315,10 +311,8 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
   const size_t far_c_off = (size_t)A.B * ldt;
   double nxp = 0.0, nxc = 0.0;  // far sums of the next target, loaded a step ahead
   if (s > 1 && l == 0) {
-    for (int kq = 0; kq < A.ksplit; ++kq) {
-      nxp += farP[kq * far_q_stride];
-      nxc += farP[kq * far_q_stride + far_c_off];
-    }
+    nxp = sum_parts(farP, A.ksplit, far_q_stride);
+    nxc = sum_parts(farP + far_c_off, A.ksplit, far_q_stride);
   }
   bool reported = false;
   __syncthreads();
@@ -354,10 +348,8 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
     sc = fma(cns[i], F0c, sc);
     nxp = nxc = 0.0;
     if (s > 1 && i + 1 < nb && l == 0) {
-      for (int kq = 0; kq < A.ksplit; ++kq) {
-        nxp += farP[kq * far_q_stride + (size_t)(i + 1) * ldt];
-        nxc += farP[kq * far_q_stride + far_c_off + (size_t)(i + 1) * ldt];
-      }
+      nxp = sum_parts(farP + (size_t)(i + 1) * ldt, A.ksplit, far_q_stride);
+      nxc = sum_parts(farP + far_c_off + (size_t)(i + 1) * ldt, A.ksplit, far_q_stride);
     }
     const double t1 = (double)(n + 1) * h;
     const double yp = fma(hh, sp, y0c);
@@ -381,7 +373,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
       if (n + 1 <= Ntraj) {
         A.Y[((size_t)traj * A.ldY + (n + 1)) * D + c] = y;
         if (A.YP) A.YP[((size_t)traj * A.ldY + (n + 1)) * D + c] = yp;
-        if (!reported && !(isfinite(y) && isfinite(fy))) {
+        if (!reported && !(finite_bits(y) && finite_bits(fy))) {
           report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
           reported = true;
         }

@@ -21,6 +21,20 @@ __device__ __forceinline__ void report_status(unsigned long long* status, int co
   atomicCAS(status, 0ull, w);
 }
 
+// x is neither infinite nor NaN: an exponent-bit test on the integer pipe
+// (GB300's FP64 pipe is the bottleneck of the sequential steps).
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
+// Sum of ks FP64 partials p[0], p[stride], ...: starts from the first one (an
+// explicit 0.0 + p[0] would cost an FP64 add).
+__device__ __forceinline__ double sum_parts(const double* p, int ks, size_t stride) {
+  double v = p[0];
+  for (int q = 1; q < ks; ++q) v += p[q * stride];
+  return v;
+}
+
 // Parameters of one trajectory passed by value (single-trajectory path).
 struct TrajParams {
   double p[kMaxParams];

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
             A.F[(n + 1) * D + c] = fy;
             A.Y[(n + 1) * D + c] = y;
             if (A.YP) A.YP[(n + 1) * D + c] = yp;  // lane 0 of warp c holds component c
-            if (!isfinite(y) || !isfinite(fy)) report_status(A.status, ABM_ERR_NONFINITE, 0, n + 1);
+            if (!finite_bits(y) || !finite_bits(fy)) report_status(A.status, ABM_ERR_NONFINITE, 0, n + 1);
           }
         } else if (warp == 3) {
           if (n >= 1) {
