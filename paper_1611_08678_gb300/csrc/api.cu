@@ -289,6 +289,7 @@ abm_status far_history_tc(abm_plan p, double alpha, const double* F, long long r
   TileDesc td{};
   for (int l = 0; l < kTrajPerTile; ++l) td.traj[l] = l;
   td.bucket = 0;
+  td.slot = 0;
   td.n_tile = (int)s + 64;
   CK(cudaMemcpyAsync(p->d_tiles, &td, sizeof(td), cudaMemcpyHostToDevice, st), "tile");
   const int nkb_total = (int)(s / 64);
@@ -353,6 +354,7 @@ abm_status schedule_batch(abm_plan p, int M, const double* alpha, const double* 
     }
   }
   std::stable_sort(tiles.begin(), tiles.end(), [](const TileDesc& x, const TileDesc& y) { return x.n_tile > y.n_tile; });
+  for (size_t t = 0; t < tiles.size(); ++t) tiles[t].slot = (int)t;
   if ((int)tiles.size() > p->max_tiles)
     return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": too many column tiles for this plan");
   size_t off = 0;
@@ -943,6 +945,7 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
     const long long rows = (long long)((S.tiles[t].n_tile + B - 1) / B) * B + 1;
     for (int hh = 0; hh < 2; ++hh) {
       at[2 * t + hh] = S.tiles[t];
+      at[2 * t + hh].slot = 2 * t + hh;  // the adjoint histories' pieces, tile 2t + hist
       at[2 * t + hh].f_off = (long long)off;
       off += (size_t)rows * kTrajPerTile * d;
     }

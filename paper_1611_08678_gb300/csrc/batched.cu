@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
         v[r] = pcs[pc];
       }
       __nv_bfloat16* dst = A.Fsh + (size_t)pc * A.fsh_plane +
-                           (((size_t)blockIdx.x * (A.fsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
+                           (((size_t)T.slot * (A.fsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
       *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
     }
   }
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
         v[rr] = pcs[pc];
       }
       __nv_bfloat16* dst = A.Fsh + (size_t)pc * A.fsh_plane +
-                           (((size_t)tile * (A.fsh_ld / 64) + s / 64) * ldt + part * ldc + cc) * 64 + prt * 8;
+                           (((size_t)Td.slot * (A.fsh_ld / 64) + s / 64) * ldt + part * ldc + cc) * 64 + prt * 8;
       *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
     }
   }

@@ -13,6 +13,8 @@ struct TileDesc {
   int traj[kTrajPerTile];  // trajectory index per lane, -1 = padding
   int bucket;              // alpha group
   int n_tile;              // largest N in the tile
+  int slot;                // the tile's place in the split history pieces (Fsh / Xsh): its
+                           // index in the N-sorted tile table (2t + hist for adjoint tiles)
   long long f_off;         // element offset of the tile's history in F / F32
 };
 

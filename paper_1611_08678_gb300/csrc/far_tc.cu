@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       for (int p = 0; p < NB; ++p) tc::prefetch_tmap(A.tmapF + p);
       // box coordinates of history block kb: Toeplitz block x = Lbase - s + 64 kb, history block (tile, kb)
       auto yw = [&](int kb) { return (xb0 + kb) * 128; };
-      auto yf = [&](int kb) { return (tile * A.f_kblocks + kb) * NCOL; };
+      const int slot = A.tiles[tile].slot;  // the tile's history pieces
+      auto yf = [&](int kb) { return (slot * A.f_kblocks + kb) * NCOL; };
       const uint64_t keep = tc::l2_policy_evict_last(), stream = tc::l2_policy_evict_first();
       // history block j may load once block j - FST has been consumed, Toeplitz
       // block i once block i - WST has: history loads run FST - WST blocks
