@@ -54,7 +54,7 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS = _measured_peaks()
 # DRAM bytes per launch of the dominant kernel from one ncu capture (see
 # profiles/); None when the kernel changed since the counters were taken.
 NCU_TRAFFIC = {
-    "chen_single": 7071488 + 95232,  # profiles/single_persistent_kernel_chen_N262144.md
+    "chen_single": 6780160 + 96000,  # profiles/single_persistent_kernel_chen_N262144.md
 }
 # Batched far kernel: DRAM bytes (read + write) of one captured launch over the
 # algorithmic operand bytes of that launch, per workload and precision, from
@@ -63,8 +63,8 @@ NCU_TRAFFIC = {
 # line scales it to its own average launch, since DRAM bytes grow with the
 # operand bytes.
 NCU_TRAFFIC_RATIO = {
-    "rossler_batched_bf16x6": (414420224 + 3102464) / 413564928,
-    "financial_batched_bf16x6": (577345024 + 3204864) / 575717376,
+    "rossler_batched_bf16x6": (414407168 + 2956544) / 413564928,
+    "financial_batched_bf16x6": (577394432 + 2907904) / 575717376,
 }
 
 
