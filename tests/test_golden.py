@@ -1,0 +1,77 @@
+"""Golden fixtures under ``tests/golden/`` (no GPU).
+
+* ``paper_table2.txt``: Table 2 of the paper (Section 4), the Hindmarsh-Rose
+  running times that ``bench.py`` prints beside its Hindmarsh-Rose line as
+  context; the constant in ``bench.py`` must be the paper's numbers.
+* ``oracle_snapshots.txt``: sampled oracle outputs written by
+  ``tests/golden/make_oracle_snapshots.py`` (which calls only the oracle); a
+  change to the oracle's arithmetic fails here until the snapshot is
+  regenerated on purpose.
+"""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+def _load_module(path, name):
+    spec = importlib.util.spec_from_file_location(name, path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_paper_table2_is_the_bench_context():
+    rows = _rows("paper_table2.txt")
+    assert [int(r[0]) for r in rows] == list(range(1, 8))
+    table = {int(r[1]): (float(r[2]), float(r[3])) for r in rows}
+    bench = _load_module(os.path.join(ROOT, "bench.py"), "bench_for_golden")
+    assert bench.PAPER_TABLE2_CUDA_S == {n: cuda for n, (_, cuda) in table.items()}
+    # Section 4: both running times grow with the number of steps.
+    ns = sorted(table)
+    for col in (0, 1):
+        assert all(table[a][col] < table[b][col] for a, b in zip(ns, ns[1:]))
+
+
+@pytest.fixture(scope="module")
+def snapshot_generator():
+    return _load_module(os.path.join(GOLDEN, "make_oracle_snapshots.py"), "make_oracle_snapshots")
+
+
+def test_oracle_matches_snapshots(snapshot_generator):
+    gen = snapshot_generator
+    stored = _rows("oracle_snapshots.txt")
+    assert len(stored) > 300
+    solves = {}
+    weights = {}
+    for kind, case, idx, comp, val in stored:
+        case, idx, comp, val = int(case), int(idx), int(comp), float(val)
+        if kind in ("Y", "YP"):
+            if case not in solves:
+                system, alpha, h, N, p, y0 = gen.SOLVES[case]
+                solves[case] = oracle.solve(system, alpha, h, N, p, y0)
+            Y, YP = solves[case]
+            got = (Y if kind == "Y" else YP)[idx, comp]
+            scale = max(np.abs(Y).max(), 1e-300)
+            # libm's pow/exp may differ by an ulp between hosts; 64 steps of the
+            # scheme keep that far below 1e-13 of the state's scale.
+            assert abs(got - val) <= 1e-13 * scale, (kind, case, idx, comp, got, val)
+        else:
+            alpha = gen.WEIGHT_ALPHAS[case]
+            if case not in weights:
+                weights[case] = oracle.weights(alpha, gen.WEIGHT_LAGS[-1])
+            b, a, c, g = weights[case]
+            got = {"b": b, "a": a, "c": c}[kind][idx] if kind != "g" else g
+            # binary128 evaluation rounded once to FP64: identical on every host
+            assert abs(got - val) <= 2 * np.spacing(abs(val)), (kind, alpha, idx, got, val)
