@@ -35,9 +35,22 @@ def test_library_exports_every_declared_symbol():
 
 def test_system_catalogue_dims():
     lib = abm.load()
-    assert [lib.abm_system_dim(i) for i in range(6)] == [1, 1, 3, 3, 3, 3]
-    assert [lib.abm_system_nparams(i) for i in range(6)] == [3, 9, 3, 3, 3, 3]
+    assert [lib.abm_system_dim(i) for i in range(7)] == [1, 1, 3, 3, 3, 3, 3]
+    assert [lib.abm_system_nparams(i) for i in range(7)] == [3, 9, 3, 3, 3, 3, 8]
     assert lib.abm_system_dim(17) == -1
+    assert lib.abm_system_dim(-1) == -1
+
+
+def test_system_catalogue_agrees_with_the_oracle():
+    """The library and the oracle number and size the right-hand sides alike
+    (two catalogues written separately; the tests pass system names to both)."""
+    import oracle
+    lib = abm.load()
+    assert set(abm.SYSTEMS) == set(oracle.SYSTEMS)
+    for name, sid in abm.SYSTEMS.items():
+        assert sid == oracle.SYSTEMS[name], name
+        assert lib.abm_system_dim(sid) == oracle.dim(name), name
+        assert lib.abm_system_nparams(sid) == oracle.nparams(name), name
 
 
 def test_plan_create_rejects_bad_options_before_any_cuda_call():
@@ -57,6 +70,39 @@ def test_plan_create_rejects_bad_options_before_any_cuda_call():
     assert lib.abm_plan_create(ctypes.byref(h), 99, ctypes.byref(o)) == 1
     o.tile_B = 48
     assert lib.abm_plan_create(ctypes.byref(h), 2, ctypes.byref(o)) == 6
+    assert not h.value
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("prec", 4, 1), ("prec", -1, 1), ("near_warps", 4, 1), ("near_warps", 6, 1),
+    ("far_split", -1, 1), ("far_split", 65, 1), ("near_split", 3, 1), ("near_split", 16, 1),
+    ("far_ctas", -2, 1), ("spin_timeout_cycles", -5, 1), ("tile_B", -64, 1), ("tile_B", 128, 6),
+])
+def test_plan_options_outside_their_documented_sets_are_rejected(field, value, status):
+    """Each option is checked against the values include/abm.h documents before
+    the plan touches the device: nothing is allocated and no plan is returned."""
+    lib = abm.load()
+    h = ctypes.c_void_p()
+    o = abm.PlanOpts()
+    lib.abm_plan_opts_default(ctypes.byref(o))
+    o.n_max = 16
+    setattr(o, field, value)
+    assert lib.abm_plan_create(ctypes.byref(h), 2, ctypes.byref(o)) == status
+    assert not h.value
+
+
+def test_tensor_core_precisions_need_three_components_and_64_row_tiles():
+    lib = abm.load()
+    h = ctypes.c_void_p()
+    o = abm.PlanOpts()
+    lib.abm_plan_opts_default(ctypes.byref(o))
+    o.n_max = 16
+    for prec in (2, 3):
+        o.prec = prec
+        o.tile_B = 0
+        assert lib.abm_plan_create(ctypes.byref(h), abm.SYSTEMS["linear"], ctypes.byref(o)) == 6
+        o.tile_B = 32
+        assert lib.abm_plan_create(ctypes.byref(h), abm.SYSTEMS["lorenz"], ctypes.byref(o)) == 6
     assert not h.value
 
 
