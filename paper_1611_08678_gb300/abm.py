@@ -103,6 +103,29 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _dev_f64(x, numel, name):
+    """A contiguous float64 CUDA tensor of x (copied when x is a host array, a
+    host tensor or another dtype) holding exactly numel values."""
+    torch = _torch()
+    t = torch.as_tensor(x, dtype=torch.float64, device="cuda").contiguous()
+    if t.numel() != numel:
+        raise ValueError(f"{name} holds {t.numel()} values, expected {numel}")
+    return t
+
+
+def _check_out(t, shape, name, cuda=True):
+    """Output buffers are written in place: they must already have the layout
+    the library writes (float64, contiguous, on the right side of the bus)."""
+    torch = _torch()
+    if t is None:
+        return
+    if (not torch.is_tensor(t) or t.dtype != torch.float64 or not t.is_contiguous()
+            or t.is_cuda != cuda or tuple(t.shape) != tuple(shape)):
+        where = "CUDA" if cuda else "host"
+        got = (tuple(t.shape), t.dtype, t.device) if torch.is_tensor(t) else type(t)
+        raise ValueError(f"{name} must be a contiguous float64 {where} tensor of shape {tuple(shape)}, got {got}")
+
+
 class Plan:
     """One plan = one system, workspace for n_max steps and max_batch trajectories."""
 
@@ -176,6 +199,7 @@ class Plan:
     def far_history(self, alpha, F, s, B, k_lo, k_hi, stream=None):
         torch = _torch()
         rows, cols = F.shape
+        _check_out(F, (rows, cols), "F")
         P = torch.empty(B, cols, dtype=torch.float64, device="cuda")
         C = torch.empty(B, cols, dtype=torch.float64, device="cuda")
         self._check(self.lib.abm_far_history(self.h, float(alpha), _dptr(F), rows, cols, int(s), int(B),
@@ -194,6 +218,8 @@ class Plan:
             Y = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
         if YP is None and want_yp:
             YP = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
+        _check_out(Y, (N + 1, self.d), "Y")
+        _check_out(YP, (N + 1, self.d), "YP")
         st = self.lib.abm_solve(self.h, float(alpha), float(h), int(N), p.ctypes.data_as(_dp),
                                 y.ctypes.data_as(_dp), _dptr(Y), _dptr(YP), _stream_ptr(stream))
         self._check(st, "abm_solve")
@@ -211,18 +237,18 @@ class Plan:
         hh = np.ascontiguousarray(h, dtype=np.float64)
         NN = np.ascontiguousarray(N, dtype=np.int32)
         M = al.size
-        if not torch.is_tensor(params):
-            params = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float64), device="cuda")
-        if not torch.is_tensor(y0):
-            y0 = torch.as_tensor(np.ascontiguousarray(y0, dtype=np.float64), device="cuda")
-        params = params.contiguous()
-        y0 = y0.contiguous()
+        if hh.size != M or NN.size != M:
+            raise ValueError("alpha, h and N need one entry per trajectory")
+        params = _dev_f64(params, M * self.np, "params")
+        y0 = _dev_f64(y0, M * self.d, "y0")
         if ldY is None:
             ldY = int(NN.max()) + 1
         if Y is None:
             Y = torch.zeros(M, ldY, self.d, dtype=torch.float64, device="cuda")
         if YP is None and want_yp:
             YP = torch.zeros(M, ldY, self.d, dtype=torch.float64, device="cuda")
+        _check_out(Y, (M, ldY, self.d), "Y")
+        _check_out(YP, (M, ldY, self.d), "YP")
         st = self.lib.abm_solve_batched(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
                                         NN.ctypes.data_as(_ip), _dptr(params), _dptr(y0), _dptr(Y), int(ldY),
                                         _dptr(YP), _stream_ptr(stream))
@@ -242,6 +268,8 @@ class Plan:
         hh = np.ascontiguousarray(h, dtype=np.float64)
         NN = np.ascontiguousarray(N, dtype=np.int32)
         M = al.size
+        if hh.size != M or NN.size != M:
+            raise ValueError("alpha, h and N need one entry per trajectory")
         params = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float64)) if not torch.is_tensor(params) \
             else params
         y0 = torch.as_tensor(np.ascontiguousarray(y0, dtype=np.float64)) if not torch.is_tensor(y0) else y0
@@ -249,15 +277,16 @@ class Plan:
             raise ValueError("solve_batched_host takes host tensors; use solve_batched for device tensors")
         params = params.to(torch.float64).contiguous()
         y0 = y0.to(torch.float64).contiguous()
+        if params.numel() != M * self.np or y0.numel() != M * self.d:
+            raise ValueError("params / y0 need n_params / d values per trajectory")
         if ldY is None:
             ldY = int(NN.max()) + 1
         if Y is None:
             Y = torch.zeros(M, ldY, self.d, dtype=torch.float64, pin_memory=True)
         if YP is None and want_yp:
             YP = torch.zeros(M, ldY, self.d, dtype=torch.float64, pin_memory=True)
-        for t in (Y, YP):
-            if t is not None and (t.is_cuda or not t.is_contiguous()):
-                raise ValueError("Y / YP must be contiguous host tensors")
+        _check_out(Y, (M, ldY, self.d), "Y", cuda=False)
+        _check_out(YP, (M, ldY, self.d), "YP", cuda=False)
         self._host_inputs = (params, y0)  # read by the asynchronous upload
         st = self.lib.abm_solve_batched_host(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
                                              NN.ctypes.data_as(_ip), ctypes.c_void_p(params.data_ptr()),
@@ -275,11 +304,19 @@ class Plan:
         hh = np.ascontiguousarray(h, dtype=np.float64)
         NN = np.ascontiguousarray(N, dtype=np.int32)
         M = al.size
+        if hh.size != M or NN.size != M:
+            raise ValueError("alpha, h and N need one entry per trajectory")
+        params = _dev_f64(params, M * self.np, "params")
+        y0 = _dev_f64(y0, M * self.d, "y0")
+        ldY = int(Y.shape[1]) if torch.is_tensor(Y) and Y.dim() == 3 else -1
+        _check_out(Y, (M, ldY, self.d), "Y")
+        _check_out(YP, (M, ldY, self.d), "YP")
+        dLdY = _dev_f64(dLdY, M * ldY * self.d, "dLdY")
         dp = torch.empty(M, self.np, dtype=torch.float64, device="cuda")
         dy0 = torch.empty(M, self.d, dtype=torch.float64, device="cuda")
         st = self.lib.abm_adjoint(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
-                                  NN.ctypes.data_as(_ip), _dptr(params.contiguous()), _dptr(y0.contiguous()),
-                                  _dptr(Y), _dptr(YP), int(Y.shape[1]), _dptr(dLdY.contiguous()), _dptr(dp),
+                                  NN.ctypes.data_as(_ip), _dptr(params), _dptr(y0),
+                                  _dptr(Y), _dptr(YP), ldY, _dptr(dLdY), _dptr(dp),
                                   _dptr(dy0), _stream_ptr(stream))
         self._check(st, "abm_adjoint")
         if sync:
@@ -294,6 +331,11 @@ def solve_noalloc(system: str, alpha, h, N, params, y0, Y, YP=None, stream=None)
     lib = load()
     p = np.ascontiguousarray(params, dtype=np.float64)
     y = np.ascontiguousarray(y0, dtype=np.float64)
+    d = lib.abm_system_dim(SYSTEMS[system])
+    if p.size != lib.abm_system_nparams(SYSTEMS[system]) or y.size != d:
+        raise ValueError("params / y0 have the wrong size for this system")
+    _check_out(Y, (N + 1, d), "Y")
+    _check_out(YP, (N + 1, d), "YP")
     buf = ctypes.create_string_buffer(256)
     st = lib.abm_solve_noalloc(SYSTEMS[system], float(alpha), float(h), int(N), p.ctypes.data_as(_dp),
                                y.ctypes.data_as(_dp), _dptr(Y), _dptr(YP), _stream_ptr(stream), buf, 256)

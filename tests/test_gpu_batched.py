@@ -92,6 +92,36 @@ def test_batched_rejects_bad_arguments(abm):
         plan.solve_batched(big.alpha, big.h, big.N, big.params, big.y0)
 
 
+def test_binding_converts_inputs_and_checks_output_buffers(abm):
+    """Inputs in any float dtype or on the host are copied to float64 CUDA
+    tensors before the call; output buffers with the wrong shape, dtype, side
+    of the bus or layout are refused before anything is launched."""
+    batch = workloads.random_batch("lorenz", 6, 40, 80, [0.9])
+    plan = abm.Plan("lorenz", n_max=80, max_batch=6)
+    ref = plan.solve_batched(batch.alpha, batch.h, batch.N, batch.params, batch.y0).cpu().numpy()
+    host_t = plan.solve_batched(batch.alpha, batch.h, batch.N, torch.as_tensor(batch.params),
+                                torch.as_tensor(batch.y0)).cpu().numpy()
+    assert np.array_equal(host_t, ref)
+    p32 = torch.as_tensor(batch.params, dtype=torch.float32, device="cuda")
+    want = plan.solve_batched(batch.alpha, batch.h, batch.N, p32.double(), batch.y0).cpu().numpy()
+    got = plan.solve_batched(batch.alpha, batch.h, batch.N, p32, batch.y0).cpu().numpy()
+    assert np.array_equal(got, want)
+    with pytest.raises(ValueError):
+        plan.solve_batched(batch.alpha, batch.h, batch.N, batch.params[:5], batch.y0)
+    with pytest.raises(ValueError):
+        plan.solve_batched(batch.alpha, batch.h[:5], batch.N, batch.params, batch.y0)
+    ldY = int(batch.N.max()) + 1
+    for Y in (torch.zeros(6, ldY, 3, dtype=torch.float32, device="cuda"),
+              torch.zeros(6, ldY, 3, dtype=torch.float64),
+              torch.zeros(6, ldY + 1, 3, dtype=torch.float64, device="cuda"),
+              torch.zeros(3, ldY, 6, dtype=torch.float64, device="cuda").transpose(0, 2)):
+        with pytest.raises(ValueError):
+            plan.solve_batched(batch.alpha, batch.h, batch.N, batch.params, batch.y0, Y=Y, ldY=ldY)
+    with pytest.raises(ValueError):
+        plan.solve(0.9, 0.01, 80, batch.params[0], batch.y0[0], Y=torch.zeros(80, 3, dtype=torch.float64,
+                                                                               device="cuda"))
+
+
 @pytest.mark.parametrize("prec,tol", [("bf16x6", 2e-6), ("bf16x3", 2e-4)])
 @pytest.mark.parametrize("s", [64, 128, 576, 4096, 8192])
 @pytest.mark.parametrize("data", ["normal", "smooth", "spread"])
