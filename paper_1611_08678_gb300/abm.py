@@ -113,17 +113,23 @@ def _dev_f64(x, numel, name):
     return t
 
 
-def _check_out(t, shape, name, cuda=True):
+def _check_out(t, shape, name, cuda=True, more_rows=False):
     """Output buffers are written in place: they must already have the layout
-    the library writes (float64, contiguous, on the right side of the bus)."""
+    the library writes (float64, contiguous, on the right side of the bus).
+    more_rows: the first dimension may be longer than the rows written."""
     torch = _torch()
     if t is None:
         return
-    if (not torch.is_tensor(t) or t.dtype != torch.float64 or not t.is_contiguous()
-            or t.is_cuda != cuda or tuple(t.shape) != tuple(shape)):
+    ok = (torch.is_tensor(t) and t.dtype == torch.float64 and t.is_contiguous() and t.is_cuda == cuda
+          and t.dim() == len(shape))
+    if ok:
+        ok = (t.shape[0] >= shape[0] if more_rows else t.shape[0] == shape[0]) and \
+            tuple(t.shape[1:]) == tuple(shape[1:])
+    if not ok:
         where = "CUDA" if cuda else "host"
+        want = f"{tuple(shape)}{' (or more rows)' if more_rows else ''}"
         got = (tuple(t.shape), t.dtype, t.device) if torch.is_tensor(t) else type(t)
-        raise ValueError(f"{name} must be a contiguous float64 {where} tensor of shape {tuple(shape)}, got {got}")
+        raise ValueError(f"{name} must be a contiguous float64 {where} tensor of shape {want}, got {got}")
 
 
 class Plan:
@@ -218,8 +224,8 @@ class Plan:
             Y = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
         if YP is None and want_yp:
             YP = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
-        _check_out(Y, (N + 1, self.d), "Y")
-        _check_out(YP, (N + 1, self.d), "YP")
+        _check_out(Y, (N + 1, self.d), "Y", more_rows=True)
+        _check_out(YP, (N + 1, self.d), "YP", more_rows=True)
         st = self.lib.abm_solve(self.h, float(alpha), float(h), int(N), p.ctypes.data_as(_dp),
                                 y.ctypes.data_as(_dp), _dptr(Y), _dptr(YP), _stream_ptr(stream))
         self._check(st, "abm_solve")
@@ -334,8 +340,8 @@ def solve_noalloc(system: str, alpha, h, N, params, y0, Y, YP=None, stream=None)
     d = lib.abm_system_dim(SYSTEMS[system])
     if p.size != lib.abm_system_nparams(SYSTEMS[system]) or y.size != d:
         raise ValueError("params / y0 have the wrong size for this system")
-    _check_out(Y, (N + 1, d), "Y")
-    _check_out(YP, (N + 1, d), "YP")
+    _check_out(Y, (N + 1, d), "Y", more_rows=True)
+    _check_out(YP, (N + 1, d), "YP", more_rows=True)
     buf = ctypes.create_string_buffer(256)
     st = lib.abm_solve_noalloc(SYSTEMS[system], float(alpha), float(h), int(N), p.ctypes.data_as(_dp),
                                y.ctypes.data_as(_dp), _dptr(Y), _dptr(YP), _stream_ptr(stream), buf, 256)

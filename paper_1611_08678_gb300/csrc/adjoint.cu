@@ -21,6 +21,7 @@
 // FP64) produce the far sums, and the near kernel below runs the reverse
 // steps with the window lags in FP64.
 #include "batched.cuh"
+#include "bf16split.cuh"
 #include "common.cuh"
 #include "systems.cuh"
 
@@ -28,13 +29,6 @@ namespace abm {
 
 
 namespace {
-__device__ __forceinline__ void split3_bf16_adj(double x, __nv_bfloat16* out) {
-  out[0] = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(out[0]);
-  out[1] = __double2bfloat16(r);
-  r -= (double)__bfloat162float(out[1]);
-  out[2] = __double2bfloat16(r);
-}
 template <int D>
 __device__ __forceinline__ void bar_components() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
@@ -280,21 +274,23 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) adjoint_near_kern
     __syncthreads();
     // BF16 split rows s..s+63 of both histories: K block s / 64 of adjoint
     // tiles 2 tile + hist (K-block tiled like the forward history pieces)
-    constexpr int UNITS = 2 * 3 * ld * 8;
+    constexpr int UNITS = 2 * ld * 8;  // (history, column, 8 rows), split once, 3 stores
     for (int u = threadIdx.x; u < UNITS; u += NT) {
-      const int hist = u / (3 * ld * 8), rem0 = u % (3 * ld * 8);
-      const int pc = rem0 / (ld * 8), rem = rem0 % (ld * 8);
+      const int hist = u / (ld * 8), rem = u % (ld * 8);
       const int cc = rem / 8, part = rem % 8;
-      __align__(16) __nv_bfloat16 v[8];
+      __align__(16) __nv_bfloat16 v[3][8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         __nv_bfloat16 pcs[3];
-        split3_bf16_adj(hist == 0 ? Wm[part * 8 + r][cc] : Wl[part * 8 + r][cc], pcs);
-        v[r] = pcs[pc];
+        split3_bf16(hist == 0 ? Wm[part * 8 + r][cc] : Wl[part * 8 + r][cc], pcs);
+        v[0][r] = pcs[0];
+        v[1][r] = pcs[1];
+        v[2][r] = pcs[2];
       }
-      __nv_bfloat16* dst = A.Xsh + (size_t)pc * A.xsh_plane +
-                           (((size_t)(2 * tile + hist) * (A.xsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
-      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+      const size_t off = (((size_t)(2 * tile + hist) * (A.xsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        *reinterpret_cast<uint4*>(A.Xsh + (size_t)pc * A.xsh_plane + off) = *reinterpret_cast<const uint4*>(v[pc]);
     }
   }
 }
@@ -449,22 +445,24 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_near_split_kernel(Ad
   }
   if (A.Xsh) {
     // BF16 split of rows s..s+63 of both histories, this CTA's columns
-    constexpr int UNITS = 2 * 3 * ldc * 8;
+    constexpr int UNITS = 2 * ldc * 8;  // (history, column, 8 rows), split once, 3 stores
     for (int u = threadIdx.x; u < UNITS; u += NT) {
-      const int hist = u / (3 * ldc * 8), rem0 = u % (3 * ldc * 8);
-      const int pc = rem0 / (ldc * 8), rem = rem0 % (ldc * 8);
+      const int hist = u / (ldc * 8), rem = u % (ldc * 8);
       const int cc = rem / 8, prt = rem % 8;
-      __align__(16) __nv_bfloat16 v[8];
+      __align__(16) __nv_bfloat16 v[3][8];
 #pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
         __nv_bfloat16 pcs[3];
-        split3_bf16_adj(hist == 0 ? Wm[prt * 8 + rr][cc] : Wl[prt * 8 + rr][cc], pcs);
-        v[rr] = pcs[pc];
+        split3_bf16(hist == 0 ? Wm[prt * 8 + rr][cc] : Wl[prt * 8 + rr][cc], pcs);
+        v[0][rr] = pcs[0];
+        v[1][rr] = pcs[1];
+        v[2][rr] = pcs[2];
       }
-      __nv_bfloat16* dst = A.Xsh + (size_t)pc * A.xsh_plane +
-                           (((size_t)(2 * tile + hist) * (A.xsh_ld / 64) + s / 64) * ld + part * ldc + cc) * 64 +
-                           prt * 8;
-      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+      const size_t off =
+          (((size_t)(2 * tile + hist) * (A.xsh_ld / 64) + s / 64) * ld + part * ldc + cc) * 64 + prt * 8;
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        *reinterpret_cast<uint4*>(A.Xsh + (size_t)pc * A.xsh_plane + off) = *reinterpret_cast<const uint4*>(v[pc]);
     }
   }
 }

@@ -12,6 +12,7 @@
 //   k = 0 terms b_n f_0, c_n f_0 : near kernel, FP64
 // (Sec. 2 formulas; the split is the per-tile form of the partial sums the
 // paper gathers across processes, Sec. 3 Fig. 2.)
+#include "bf16split.cuh"
 #include "common.cuh"
 #include "systems.cuh"
 #include "batched.cuh"
@@ -71,14 +72,6 @@ __global__ void batched_setup_kernel(BatchArgs A) {
 // helpers, each chain warp sums its whole window itself (fewer instructions;
 // best when several tiles share an SM and hide each other's latency).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void split3_bf16(double x, __nv_bfloat16* out) {
-  out[0] = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(out[0]);
-  out[1] = __double2bfloat16(r);
-  r -= (double)__bfloat162float(out[1]);
-  out[2] = __double2bfloat16(r);
-}
-
 template <int SYS, int HS>
 __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kernel(BatchArgs A, long long s, int nb) {
   using S = Sys<SYS>;
@@ -234,23 +227,26 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
   __syncthreads();
   if (A.Fsh) {
     // BF16 split of rows s..s+63 = K block s / 64 of this column tile (K-block
-    // tiled, K-major inside): 8 rows of one column and piece per 16-byte store
-    // (row s of the first tile stays zero: the j = 0 term is FP64)
-    constexpr int UNITS = 3 * ld * 8;
+    // tiled, K-major inside): a unit is 8 rows of one column, split once and
+    // stored as one 16-byte chunk per piece (row s of the first tile stays
+    // zero: the j = 0 term is FP64)
+    constexpr int UNITS = ld * 8;
     for (int u = threadIdx.x; u < UNITS; u += NT) {
-      const int pc = u / (ld * 8), rem = u % (ld * 8);
-      const int cc = rem / 8, part = rem % 8;
-      __align__(16) __nv_bfloat16 v[8];
+      const int cc = u / 8, part = u % 8;
+      __align__(16) __nv_bfloat16 v[3][8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int row = part * 8 + r;
         __nv_bfloat16 pcs[3];
         split3_bf16((s == 0 && row == 0) ? 0.0 : Fw[row][cc], pcs);
-        v[r] = pcs[pc];
+        v[0][r] = pcs[0];
+        v[1][r] = pcs[1];
+        v[2][r] = pcs[2];
       }
-      __nv_bfloat16* dst = A.Fsh + (size_t)pc * A.fsh_plane +
-                           (((size_t)T.slot * (A.fsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
-      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+      const size_t off = (((size_t)T.slot * (A.fsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        *reinterpret_cast<uint4*>(A.Fsh + (size_t)pc * A.fsh_plane + off) = *reinterpret_cast<const uint4*>(v[pc]);
     }
   }
 }
@@ -383,23 +379,25 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
   }
   if (A.Fsh) {
     // BF16 split of rows s..s+63 of this CTA's columns (layout as in
-    // batched_near_kernel: K-block tiled, 8 rows of one column and piece per
-    // 16-byte store; row s of the first tile stays zero)
-    constexpr int UNITS = 3 * ldc * 8;
+    // batched_near_kernel: K-block tiled, a unit is 8 rows of one column split
+    // once, one 16-byte store per piece; row s of the first tile stays zero)
+    constexpr int UNITS = ldc * 8;
     for (int u = threadIdx.x; u < UNITS; u += NT) {
-      const int pc = u / (ldc * 8), rem = u % (ldc * 8);
-      const int cc = rem / 8, prt = rem % 8;
-      __align__(16) __nv_bfloat16 v[8];
+      const int cc = u / 8, prt = u % 8;
+      __align__(16) __nv_bfloat16 v[3][8];
 #pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
         const int row = prt * 8 + rr;
         __nv_bfloat16 pcs[3];
         split3_bf16((s == 0 && row == 0) ? 0.0 : Fw[row][cc], pcs);
-        v[rr] = pcs[pc];
+        v[0][rr] = pcs[0];
+        v[1][rr] = pcs[1];
+        v[2][rr] = pcs[2];
       }
-      __nv_bfloat16* dst = A.Fsh + (size_t)pc * A.fsh_plane +
-                           (((size_t)Td.slot * (A.fsh_ld / 64) + s / 64) * ldt + part * ldc + cc) * 64 + prt * 8;
-      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+      const size_t off = (((size_t)Td.slot * (A.fsh_ld / 64) + s / 64) * ldt + part * ldc + cc) * 64 + prt * 8;
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        *reinterpret_cast<uint4*>(A.Fsh + (size_t)pc * A.fsh_plane + off) = *reinterpret_cast<const uint4*>(v[pc]);
     }
   }
 }

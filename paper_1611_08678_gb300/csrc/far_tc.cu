@@ -50,6 +50,7 @@
 #include <cudaTypedefs.h>
 
 #include "batched.cuh"
+#include "bf16split.cuh"
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -75,13 +76,6 @@ template <> struct FarKind<3> {
 template <> struct FarKind<6> {
   static constexpr int NPROD = 6, NP = 3, WST = 2, FST = 3, CB = 2, NBUF = 3;
 };
-__device__ __forceinline__ void split3(double x, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
-  hi = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(hi);
-  mid = __double2bfloat16(r);
-  r -= (double)__bfloat162float(mid);
-  lo = __double2bfloat16(r);
-}
 
 }  // namespace
 
@@ -95,12 +89,12 @@ __global__ void build_wx_kernel(const double* __restrict__ b, const double* __re
   const long long lag = Lbase - x + (r & 63);
   double w = 0.0;
   if (lag >= 0 && lag <= Mw) w = (r < 64) ? b[lag] : a[lag];
-  __nv_bfloat16 hi, mid, lo;
-  split3(w, hi, mid, lo);
+  __nv_bfloat16 pcs[3];
+  split3_bf16(w, pcs);
   const size_t plane = (size_t)128 * Lx;
-  Wx[idx] = hi;
-  Wx[plane + idx] = mid;
-  Wx[2 * plane + idx] = lo;
+  Wx[idx] = pcs[0];
+  Wx[plane + idx] = pcs[1];
+  Wx[2 * plane + idx] = pcs[2];
 }
 
 
@@ -315,10 +309,9 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       const int r = lq * 32 + lane;    // accumulator row: 0..63 predictor, 64..127 corrector
       const int half = r >> 6, i = r & 63;
       double* out = A.far + (((size_t)tile * 2 + half) * 64 + i) * NCOL + cg * ECOLS;
-      auto col = [&](int j) {  // column j's sum: hi + lo of its half of the pair
+      auto col = [&](int j) {  // column j's sum: hi + lo of its half of the pair (one FP64 add)
         const int sh = (j & 1) * 32;
-        return (double)__uint_as_float((uint32_t)(hi[j >> 1] >> sh)) +
-               (double)__uint_as_float((uint32_t)(lo[j >> 1] >> sh));
+        return f32_bits_to_f64((uint32_t)(hi[j >> 1] >> sh)) + f32_bits_to_f64((uint32_t)(lo[j >> 1] >> sh));
       };
       if (A.ksplit == 1) {
 #pragma unroll
@@ -341,12 +334,12 @@ __global__ void fill_fsh_kernel(const double* __restrict__ F, long long s, __nv_
   if (idx >= s * NCOL) return;
   const long long k = idx / NCOL;
   const int col = (int)(idx % NCOL);
-  __nv_bfloat16 hi, mid, lo;
-  split3(k == 0 ? 0.0 : F[idx], hi, mid, lo);
+  __nv_bfloat16 pcs[3];
+  split3_bf16(k == 0 ? 0.0 : F[idx], pcs);
   const size_t o = ((size_t)(k >> 6) * NCOL + col) * 64 + (k & 63);  // K-block tiled, column tile 0
-  Fsh[o] = hi;
-  Fsh[plane + o] = mid;
-  Fsh[2 * plane + o] = lo;
+  Fsh[o] = pcs[0];
+  Fsh[plane + o] = pcs[1];
+  Fsh[2 * plane + o] = pcs[2];
 }
 
 // P[i][col] / C[i][col] = sum over the K-split partials of column tile 0.

@@ -120,6 +120,9 @@ def test_binding_converts_inputs_and_checks_output_buffers(abm):
     with pytest.raises(ValueError):
         plan.solve(0.9, 0.01, 80, batch.params[0], batch.y0[0], Y=torch.zeros(80, 3, dtype=torch.float64,
                                                                                device="cuda"))
+    Ylong = torch.zeros(90, 3, dtype=torch.float64, device="cuda")  # longer buffers are fine
+    plan.solve(0.9, 0.01, 80, batch.params[0], batch.y0[0], Y=Ylong)
+    assert bool(torch.all(Ylong[81:] == 0)) and bool(torch.all(Ylong[:81, 0] != 0))
 
 
 @pytest.mark.parametrize("prec,tol", [("bf16x6", 2e-6), ("bf16x3", 2e-4)])
