@@ -63,8 +63,8 @@ NCU_TRAFFIC = {
 # line scales it to its own average launch, since DRAM bytes grow with the
 # operand bytes.
 NCU_TRAFFIC_RATIO = {
-    "rossler_batched_bf16x6": (414407168 + 2956544) / 413564928,
-    "financial_batched_bf16x6": (577394432 + 2907904) / 575717376,
+    "rossler_batched_bf16x6": (414428928 + 3322880) / 413564928,
+    "financial_batched_bf16x6": (385732352 + 3349248) / 384024576,
 }
 
 
