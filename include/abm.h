@@ -81,10 +81,13 @@ typedef enum {
   ABM_PREC_BF16X3_FAR = 2, /* far history on the tensor cores (tcgen05): each
                              operand split into three BF16 pieces
                              x = hi + mid + lo, the three largest cross products
-                             hi*hi + hi*mid + mid*hi, FP32 accumulation over at
-                             most 512 rows, compensated FP32 sums beyond     */
+                             hi*hi + hi*mid + mid*hi, FP32 accumulation of
+                             the leading product over 256 history rows, a
+                             compensated FP32 sum beyond, FP64 at the end    */
   ABM_PREC_BF16X6_FAR = 3  /* as BF16X3 with all six products down to 2^-24
-                             (adds hi*lo, mid*mid, lo*hi): FP32-level error    */
+                             (adds hi*lo, mid*mid, lo*hi) and the leading
+                             product accumulated over 128 rows: FP32-level
+                             error                                            */
 } abm_precision;
 
 typedef struct abm_plan_s* abm_plan;
@@ -134,9 +137,12 @@ int abm_system_nparams(abm_system sys);
 
 /* Creates a plan for one system.  Allocates the workspace for n_max steps and
  * max_batch trajectories on the current device.  ABM_ERR_INVALID_ARG for
- * n_max < 1, negative sizes or nonzero reserved fields; ABM_ERR_OOM when the
- * workspace does not fit; ABM_ERR_UNSUPPORTED for a tensor-core precision
- * (BF16X3, BF16X6) with a system of dimension 1. */
+ * n_max < 1, negative sizes, an unknown system or precision, an option outside
+ * the values documented above or nonzero reserved fields (all checked before
+ * any CUDA call; *out stays NULL); ABM_ERR_OOM when the workspace does not
+ * fit; ABM_ERR_UNSUPPORTED for tile_B other than 0, 32 or 64, and for a
+ * tensor-core precision (BF16X3, BF16X6) with a system of dimension 1 or with
+ * tile_B = 32. */
 abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o);
 
 /* Frees the plan and its workspace (synchronises the device first). */
