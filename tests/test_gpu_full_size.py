@@ -1,0 +1,105 @@
+"""GPU parity at the full benchmark sizes, in the launch configuration the
+benchmark times (BF16x6 far history, default plan options), through the C ABI.
+
+The oracle cannot run whole workloads, so each test checks sampled outputs it
+can compute one by one (trajectories stratified by N, pointwise over t <= 5,
+or one trajectory's full gradient), and properties that hold at any size for
+every trajectory: finite states on rows 0..N_i and untouched rows beyond.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1611_08678_gb300 import workloads
+from tests._metrics import rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def abm():
+    from paper_1611_08678_gb300 import abm as m
+    m.load()
+    return m
+
+
+def _solve_full(abm, w):
+    ldY = int(w.N.max()) + 1
+    plan = abm.Plan(w.system, n_max=ldY - 1, max_batch=w.M, prec="bf16x6")
+    Y = torch.zeros(w.M, ldY, w.d, dtype=torch.float64, device="cuda")
+    plan.solve_batched(w.alpha, w.h, w.N, torch.as_tensor(w.params, device="cuda"),
+                       torch.as_tensor(w.y0, device="cuda"), Y=Y, ldY=ldY)
+    plan.close()
+    return Y
+
+
+def _check_rows(w, Y):
+    """Rows 0..N_i finite, rows beyond N_i still zero, row 0 = y0 (any size)."""
+    ldY = Y.shape[1]
+    Nt = torch.as_tensor(w.N, device="cuda")
+    inside = torch.arange(ldY, device="cuda")[None, :] <= Nt[:, None]  # (M, ldY)
+    finite_rows = torch.isfinite(Y).all(dim=2)
+    assert bool(finite_rows[inside].all())
+    del finite_rows
+    zero_rows = (Y == 0).all(dim=2)
+    assert bool(zero_rows[~inside].all())
+    del zero_rows
+    assert torch.equal(Y[:, 0, :].cpu(), torch.as_tensor(w.y0))
+
+
+def _sampled_pointwise(w, Y, n_sub, t_win=5.0):
+    order = np.argsort(w.N, kind="stable")
+    pick = order[np.linspace(0, w.M - 1, n_sub).astype(int)]
+    errs = []
+    for i in pick:
+        n = min(int(w.N[i]), int(round(t_win / w.h[i])))
+        ref = oracle.solve(w.system, float(w.alpha[i]), float(w.h[i]), n, w.params[i], w.y0[i])[0]
+        errs.append(rel_err(Y[i, : n + 1].cpu().numpy(), ref))
+    return max(errs)
+
+
+def test_rossler_full_workload(abm):
+    """4096 trajectories, ragged N log-uniform in [2^12, 2^16], 8 alpha groups."""
+    w = workloads.rossler_batched()
+    Y = _solve_full(abm, w)
+    _check_rows(w, Y)
+    err = _sampled_pointwise(w, Y, 16)
+    print(f"rossler full size, 16 sampled trajectories, t <= 5: {err:.3e}")
+    assert err <= 1e-6
+
+
+def test_financial_full_workload(abm):
+    """16384 trajectories x 2^16 steps (Y alone is 25.8 GB)."""
+    w = workloads.financial_batched()
+    Y = _solve_full(abm, w)
+    _check_rows(w, Y)
+    err = _sampled_pointwise(w, Y, 8)
+    print(f"financial full size, 8 sampled trajectories, t <= 5: {err:.3e}")
+    assert err <= 1e-6
+
+
+def test_lorenz_adjoint_full_workload(abm):
+    """1024 trajectories x 2^14 steps: forward + adjoint as timed, the first
+    trajectory's gradient against the oracle's tangent-linear gradient."""
+    w, tparams = workloads.lorenz_adjoint()
+    N, M, d = int(w.N.max()), w.M, w.d
+    plan = abm.Plan("lorenz", n_max=N, max_batch=M, prec="bf16x6")
+    params = torch.as_tensor(w.params, device="cuda")
+    y0 = torch.as_tensor(w.y0, device="cuda")
+    Y = torch.zeros(M, N + 1, d, dtype=torch.float64, device="cuda")
+    YP = torch.zeros_like(Y)
+    Yt = plan.solve_batched(w.alpha, w.h, w.N, torch.as_tensor(tparams, device="cuda"), y0)
+    plan.solve_batched(w.alpha, w.h, w.N, params, y0, Y=Y, YP=YP)
+    scale = 2.0 / ((N + 1) * d)
+    G = (Y - Yt) * scale
+    dp, dy0 = plan.adjoint(w.alpha, w.h, w.N, params, y0, Y, YP, G)
+    assert bool(torch.isfinite(dp).all()) and bool(torch.isfinite(dy0).all())
+    i = 0
+    Gi = G[i].cpu().numpy()
+    op, oy = oracle.tangent("lorenz", float(w.alpha[i]), float(w.h[i]), N, w.params[i], w.y0[i], Gi)
+    dpi, dyi = dp[i].cpu().numpy(), dy0[i].cpu().numpy()
+    err = max(np.max(np.abs(dpi - op)) / np.max(np.abs(op)), np.max(np.abs(dyi - oy)) / np.max(np.abs(oy)))
+    print(f"lorenz adjoint full size, trajectory 0 gradient: {err:.3e}")
+    assert err <= 1e-5
