@@ -300,7 +300,7 @@ def bench_single(args, name, w, world, rank, local):
                                 "this_run_seconds": total_max / args.steps,
                                 "note": "paper's unnamed GPU, precision and parameters unstated: context only"}
     if rank == 0 and not args.no_cpu_baseline:
-        n_sample = min(N, 1 << 15)
+        n_sample = min(N, 1 << 16)  # about 10 s of oracle work on one host core
         cb, Yo = single_cpu_baseline(w, n_sample)
         out["cpu_baseline"] = cb
         # stated error of this run against the oracle, over its pointwise window
