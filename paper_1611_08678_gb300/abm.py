@@ -248,7 +248,7 @@ class Plan:
         params = _dev_f64(params, M * self.np, "params")
         y0 = _dev_f64(y0, M * self.d, "y0")
         if ldY is None:
-            ldY = int(NN.max()) + 1
+            ldY = int(NN.max()) + 1 if NN.size else 1  # an empty batch reaches the library's M check
         if Y is None:
             Y = torch.zeros(M, ldY, self.d, dtype=torch.float64, device="cuda")
         if YP is None and want_yp:
@@ -286,7 +286,7 @@ class Plan:
         if params.numel() != M * self.np or y0.numel() != M * self.d:
             raise ValueError("params / y0 need n_params / d values per trajectory")
         if ldY is None:
-            ldY = int(NN.max()) + 1
+            ldY = int(NN.max()) + 1 if NN.size else 1  # an empty batch reaches the library's M check
         if Y is None:
             Y = torch.zeros(M, ldY, self.d, dtype=torch.float64, pin_memory=True)
         if YP is None and want_yp:

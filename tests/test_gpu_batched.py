@@ -90,6 +90,9 @@ def test_batched_rejects_bad_arguments(abm):
     big = workloads.random_batch("lorenz", 5, 10, 20, [0.9])
     with pytest.raises(abm.AbmError):
         plan.solve_batched(big.alpha, big.h, big.N, big.params, big.y0)
+    with pytest.raises(abm.AbmError) as ei:  # an empty batch: 1 <= M is documented
+        plan.solve_batched(np.zeros(0), np.zeros(0), np.zeros(0, np.int64), np.zeros((0, 3)), np.zeros((0, 3)))
+    assert ei.value.status == 1
 
 
 def test_binding_converts_inputs_and_checks_output_buffers(abm):
