@@ -16,6 +16,10 @@ Parity status per function (each pin lives in ``tests/test_oracle.py``):
   solve        pinned: exact for y-independent linear forcing (corrector) and
                constant forcing (predictor), Mittag-Leffler convergence,
                alpha = 1 integral-form trapezoid identity, observed order.
+  solve, passes > 1 (P(EC)^m E)
+               pinned: on D^a y = lam y many passes reach the implicit
+               corrector's solution, solved in closed form step by step;
+               y-independent forcing gives the same result for every m.
   tangent      pinned: central finite differences of ``solve``.
   history      pinned: brute-force Python double loop on tiny inputs and the
                identity that it reproduces the sums inside ``solve``.
@@ -72,6 +76,8 @@ def _bind(lib):
     lib.oracle_solve.restype = I
     lib.oracle_tangent.argtypes = [I, D, D, L, _dp, _dp, _dp, _dp, _dp]
     lib.oracle_tangent.restype = I
+    lib.oracle_solve_pecm.argtypes = [I, D, D, L, _dp, _dp, I, _dp, _dp, _dp]
+    lib.oracle_solve_pecm.restype = I
     return lib
 
 
@@ -187,15 +193,21 @@ def history(b, a, c, F, n: int, k_lo: int, k_hi: int):
     return P, C
 
 
-def solve(system: str, alpha: float, h: float, N: int, params, y0, return_f: bool = False):
-    """ABM PECE solve.  Returns (Y, YP[, F]) with shape (N+1, d); Y[0] = YP[0] = y0."""
+def solve(system: str, alpha: float, h: float, N: int, params, y0, return_f: bool = False, passes: int = 1):
+    """ABM PECE solve (passes = 1), or P(EC)^m E with m = passes corrector
+    passes per step (oracle_solve_pecm).  Returns (Y, YP[, F]) with shape
+    (N+1, d); Y[0] = YP[0] = y0."""
     d = dim(system)
     p = np.ascontiguousarray(params, dtype=np.float64)
     y0a = np.ascontiguousarray(y0, dtype=np.float64).reshape(d)
     Y = np.empty((N + 1, d)); YP = np.empty((N + 1, d))
     F = np.empty((N + 1, d)) if return_f else None
-    rc = _load().oracle_solve(_sys_id(system), float(alpha), float(h), int(N), _ptr(p), _ptr(y0a),
-                              _ptr(Y), _ptr(YP), _ptr(F) if return_f else None)
+    if passes == 1:
+        rc = _load().oracle_solve(_sys_id(system), float(alpha), float(h), int(N), _ptr(p), _ptr(y0a),
+                                  _ptr(Y), _ptr(YP), _ptr(F) if return_f else None)
+    else:
+        rc = _load().oracle_solve_pecm(_sys_id(system), float(alpha), float(h), int(N), _ptr(p), _ptr(y0a),
+                                       int(passes), _ptr(Y), _ptr(YP), _ptr(F) if return_f else None)
     if rc:
         raise ValueError(f"oracle_solve failed (rc={rc})")
     return (Y, YP, F) if return_f else (Y, YP)

@@ -270,6 +270,60 @@ int oracle_solve(int sys, double alpha, double h, long N, const double* p, const
   return 0;
 }
 
+/* ---- P(EC)^m E: the same scheme with m corrector passes per step ----
+ * The corrector is an implicit equation for y_{n+1} (its last term is
+ * g f(t_{n+1}, y_{n+1})); PECE evaluates that term once, at the predictor.
+ * P(EC)^m E repeats the corrector m times, each pass evaluating f at the
+ * previous pass's value, then evaluates F_{n+1} once at the last one:
+ *   y^(0) = y^P_{n+1}
+ *   y^(j) = y_0 + h_hat * (c_n F_0 + sum_{k=1..n} a_{n-k} F_k + g f(t_{n+1}, y^(j-1))),
+ *           j = 1..m
+ *   y_{n+1} = y^(m),  F_{n+1} = f(t_{n+1}, y_{n+1}).
+ * m = 1 is the PECE of oracle_solve.  Not in the paper: a common variant of
+ * the Adams predictor-corrector, whose passes move y_{n+1} toward the
+ * solution of the implicit corrector.  YP holds y^P as in oracle_solve. */
+int oracle_solve_pecm(int sys, double alpha, double h, long N, const double* p, const double* y0,
+                      int m, double* Y, double* YP, double* Fout) {
+  int d = oracle_dim(sys);
+  if (d < 1 || !(alpha > 0.0 && alpha <= 1.0) || !(h > 0.0) || N < 1 || m < 1) return 1;
+  double *b = malloc(sizeof(double) * (N + 1)), *a = malloc(sizeof(double) * (N + 1));
+  double *c = malloc(sizeof(double) * (N + 1));
+  double* F = Fout ? Fout : malloc(sizeof(double) * (N + 1) * d);
+  if (!b || !a || !c || !F) { free(b); free(a); free(c); if (!Fout) free(F); return 2; }
+  double g;
+  oracle_weights(alpha, N, b, a, c, &g);
+  double hat = pow(h, alpha);
+  double yp[3], yj[3], fj[3], sc[3];
+  for (int i = 0; i < d; ++i) { Y[i] = y0[i]; YP[i] = y0[i]; }
+  oracle_rhs(sys, alpha, p, 0.0, y0, F);
+  for (long n = 0; n < N; ++n) {
+    double tn1 = (double)(n + 1) * h;
+    for (int i = 0; i < d; ++i) {             /* predictor, eq. (2) */
+      double sum = 0.0;
+      for (long k = 0; k <= n; ++k) sum += b[n - k] * F[k * d + i];
+      yp[i] = y0[i] + hat * sum;
+      yj[i] = yp[i];
+    }
+    for (int i = 0; i < d; ++i) {             /* corrector history part, fixed over the passes */
+      double sum = c[n] * F[i];
+      for (long k = 1; k <= n; ++k) sum += a[n - k] * F[k * d + i];
+      sc[i] = sum;
+    }
+    for (int j = 1; j <= m; ++j) {            /* m corrector passes */
+      oracle_rhs(sys, alpha, p, tn1, yj, fj);
+      for (int i = 0; i < d; ++i) yj[i] = y0[i] + hat * (sc[i] + g * fj[i]);
+    }
+    for (int i = 0; i < d; ++i) {
+      Y[(n + 1) * d + i] = yj[i];
+      YP[(n + 1) * d + i] = yp[i];
+    }
+    oracle_rhs(sys, alpha, p, tn1, Y + (n + 1) * d, F + (n + 1) * d);
+  }
+  free(b); free(a); free(c);
+  if (!Fout) free(F);
+  return 0;
+}
+
 /* ---- tangent-linear gradient of a trajectory loss ----
  * Sensitivities S_n = d y_n / d theta, theta = (p[0..np-1], y0[0..d-1]), are
  * carried through exactly the same discrete scheme (differentiate every line

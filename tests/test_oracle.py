@@ -181,6 +181,69 @@ def test_mittag_leffler(alpha, lam):
         assert abs(math.log2(errs[1] / errs[2]) / 2.0 - 2.0) < 0.1
 
 
+def _pecm_linear(alpha, h, N, lam, y0, m):
+    """P(EC)^m E on D^a y = lam y in closed form per step.  With the history
+    part A = y0 + h^a (c_n F_0 + sum_{k=1..n} a_{n-k} F_k) and B = h^a g lam,
+    every pass maps y to A + B y, so m passes from the predictor y^P give
+    A (1 - B^m) / (1 - B) + B^m y^P (m = inf: the implicit corrector's
+    solution A / (1 - B))."""
+    b, a, c, g = oracle.weights(alpha, N)
+    hh = h ** alpha
+    Y = np.empty(N + 1)
+    Y[0] = y0
+    F = [lam * y0]
+    B = hh * g * lam
+    for n in range(N):
+        yp = y0 + hh * sum(b[n - k] * F[k] for k in range(n + 1))
+        A = y0 + hh * (c[n] * F[0] + sum(a[n - k] * F[k] for k in range(1, n + 1)))
+        y = A / (1.0 - B) if m is None else A * (1.0 - B ** m) / (1.0 - B) + B ** m * yp
+        Y[n + 1] = y
+        F.append(lam * y)
+    return Y
+
+
+@pytest.mark.parametrize("alpha,h,lam", [(0.6, 0.05, -2.0), (0.9, 0.02, 1.5), (1.0, 0.05, -3.0)])
+@pytest.mark.parametrize("m", [1, 2, 3, 5])
+def test_pecm_matches_closed_form_passes(alpha, h, lam, m):
+    """Finite m: the pass count is exact (one pass more or less fails)."""
+    N, y0 = 120, 0.8
+    Y, _ = oracle.solve("linear", alpha, h, N, [lam, 0.0, 0.0], [y0], passes=m)
+    ref = _pecm_linear(alpha, h, N, lam, y0, m)
+    assert np.max(np.abs(Y[:, 0] - ref)) <= 1e-13 * np.abs(ref).max()
+    if m > 1:
+        other = _pecm_linear(alpha, h, N, lam, y0, m - 1)
+        assert np.max(np.abs(Y[:, 0] - other)) > 1e-10 * np.abs(ref).max()
+
+
+def test_pecm_converges_to_the_implicit_corrector():
+    """Many passes reach the solution of the implicit corrector (|B| < 1)."""
+    N, y0, alpha, h, lam = 150, 1.0, 0.7, 0.05, -2.0
+    Y, _ = oracle.solve("linear", alpha, h, N, [lam, 0.0, 0.0], [y0], passes=60)
+    ref = _pecm_linear(alpha, h, N, lam, y0, None)
+    assert np.max(np.abs(Y[:, 0] - ref)) <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_pecm_y_independent_forcing_is_unchanged(m):
+    """With f independent of y every pass returns the same value: P(EC)^m E
+    equals PECE exactly, and both stay exact for linear forcing."""
+    N, alpha, h, q0, q1, y0 = 200, 0.5, 0.03, 1.3, -0.7, 0.25
+    Y1, YP1 = oracle.solve("linear", alpha, h, N, [0.0, q0, q1], [y0])
+    Ym, YPm = oracle.solve("linear", alpha, h, N, [0.0, q0, q1], [y0], passes=m)
+    assert np.array_equal(Y1, Ym) and np.array_equal(YP1, YPm)
+
+
+def test_pecm_one_pass_is_pece():
+    """The P(EC)^m E routine itself with m = 1 reproduces the PECE solve."""
+    N, p, y0 = 300, np.array([10.0, 28.0, 8 / 3]), np.array([0.1, 0.1, 0.1])
+    Y1, YP1 = oracle.solve("lorenz", 0.9, 0.01, N, p, y0)
+    Ym, YPm = np.empty((N + 1, 3)), np.empty((N + 1, 3))
+    rc = oracle._load().oracle_solve_pecm(oracle.SYSTEMS["lorenz"], 0.9, 0.01, N, oracle._ptr(p),
+                                          oracle._ptr(y0), 1, oracle._ptr(Ym), oracle._ptr(YPm), None)
+    assert rc == 0
+    assert np.array_equal(Y1, Ym) and np.array_equal(YP1, YPm)
+
+
 def _integral_trapezoid(system, h, N, p, y0):
     """alpha = 1: rectangle predictor / trapezoid corrector in integral form,
     written independently of the oracle's weight machinery."""
@@ -377,6 +440,9 @@ MUTANTS = {
     "time_index": ("double t1 = (double)(n + 1) * h;\n    for (int i = 0; i < d; ++i) {             /* predictor",
                    "double t1 = (double)n * h;\n    for (int i = 0; i < d; ++i) {             /* predictor"),
     "lorenz_transposed": ("f[1] = y[0] * (p[1] - y[2]) - y[1];", "f[1] = y[1] * (p[1] - y[2]) - y[0];"),
+    # P(EC)^m E: one pass short, and every pass evaluated at the predictor
+    "pecm_pass_count": ("for (int j = 1; j <= m; ++j) {", "for (int j = 1; j < m; ++j) {"),
+    "pecm_stale_state": ("oracle_rhs(sys, alpha, p, tn1, yj, fj);", "oracle_rhs(sys, alpha, p, tn1, yp, fj);"),
 }
 
 
@@ -390,6 +456,7 @@ def _pins_pass():
         lambda: test_alpha_one_is_integral_form_trapezoid("lorenz", [10.0, 28.0, 8.0 / 3.0], [0.1, 0.1, 0.1]),
         lambda: test_mittag_leffler(0.9, -1.0),
         test_lorenz_divergence_is_constant,
+        lambda: test_pecm_matches_closed_form_passes(0.6, 0.05, -2.0, 3),
     ] + [lambda e=e: test_rhs_vanishes_at_equilibria(*e) for e in _equilibria()]
     for chk in checks:
         try:
