@@ -82,6 +82,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mib", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner (library defaults)")
+    ap.add_argument("--corrector-passes", type=int, default=1,
+                    help="batched: corrector passes per step (1 = PECE, m > 1 = P(EC)^m E)")
     ap.add_argument("--trajectories", type=int, default=0,
                     help="batched workloads: first M trajectories only (small cases for profiling)")
     return ap.parse_args(argv)
@@ -382,6 +384,7 @@ def bench_batched(args, name, w, prec, world, rank, local):
         from paper_1611_08678_gb300 import autotune
         tuned = autotune.tune_batched(shard, prec)  # untimed; cached per shape
     plan = abm.Plan(shard.system, n_max=int(N.max()), max_batch=shard.M, prec=prec, profile=True,
+                    corrector_passes=args.corrector_passes,
                     near_warps=tuned["near_warps"], far_split=tuned["far_split"])
     params = torch.as_tensor(shard.params, device="cuda")
     y0 = torch.as_tensor(shard.y0, device="cuda")
@@ -468,6 +471,7 @@ def bench_batched(args, name, w, prec, world, rank, local):
     # that give the roofline its kernel times
     plan.close()  # one workspace at a time
     gplan = abm.Plan(shard.system, n_max=int(N.max()), max_batch=shard.M, prec=prec, use_graph=True,
+                     corrector_passes=args.corrector_passes,
                      near_warps=tuned["near_warps"], far_split=tuned["far_split"])
     gsteps = max(1, min(args.steps, 3))
     for _ in range(2):  # capture, then one replay
@@ -490,6 +494,7 @@ def bench_batched(args, name, w, prec, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"f64 state, {prec} far",
         "data": "synthetic",
         "config": {"workload": name, "system": w.system, "trajectories": int(w.M), "trajectories_per_gpu": int(shard.M),
+                   "corrector_passes": args.corrector_passes,
                    "N_range": [int(w.N.min()), int(w.N.max())], "sum_N": int(w.N.sum()),
                    "alphas": sorted(set(float(a) for a in w.alpha)), "far_precision": prec,
                    "parallelism": f"trajectory shards x{world}",
@@ -505,11 +510,11 @@ def bench_batched(args, name, w, prec, world, rank, local):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out.update(batched_cpu_baseline(w, Y if world == 1 else None))
+        out.update(batched_cpu_baseline(w, Y if world == 1 else None, passes=args.corrector_passes))
     return out
 
 
-def batched_cpu_baseline(w, Y=None, n_sub=16):
+def batched_cpu_baseline(w, Y=None, n_sub=16, passes=1):
     """Oracle on a seeded subset (stratified by N), threads over the host
     cores; scaled by history MACs to the whole workload.  With Y (this run's
     GPU result, single rank) also the stated error over t <= 5."""
@@ -523,7 +528,8 @@ def batched_cpu_baseline(w, Y=None, n_sub=16):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
     def run(i):
-        return oracle.solve(w.system, float(w.alpha[i]), float(w.h[i]), int(w.N[i]), w.params[i], w.y0[i])[0]
+        return oracle.solve(w.system, float(w.alpha[i]), float(w.h[i]), int(w.N[i]), w.params[i], w.y0[i],
+                            passes=passes)[0]
 
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=cores) as ex:
@@ -547,7 +553,7 @@ def batched_cpu_baseline(w, Y=None, n_sub=16):
             errs.append(rel_err(Yc[i, : n + 1], ref[: n + 1]))
             nerrs.append(float(np.abs(Yc[i, : n + 1] - ref[: n + 1]).max() / np.abs(ref[: n + 1]).max()))
             y0p = np.asarray(w.y0[i], float) * (1.0 + 2.0 ** -24)
-            refp = oracle.solve(w.system, float(w.alpha[i]), float(w.h[i]), n, w.params[i], y0p)[0]
+            refp = oracle.solve(w.system, float(w.alpha[i]), float(w.h[i]), n, w.params[i], y0p, passes=passes)[0]
             cond.append(rel_err(refp, ref[: n + 1]))
         out["max_rel_err_vs_oracle"] = float(max(errs))
         out["max_normwise_err_vs_oracle"] = float(max(nerrs))

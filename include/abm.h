@@ -125,7 +125,15 @@ typedef struct {
                           largest of 8 and 4 whose CTAs fit on the SMs, else
                           none; 1 = never; 2, 4 or 8 = that split for every
                           time tile                                          */
-  int reserved[7];     /* must be zero                                            */
+  int corrector_passes; /* corrector passes per step: 0 or 1 = PECE, the scheme
+                          of Sec. 2; m = 2..8 = P(EC)^m E: the corrector, whose
+                          last term g f(t_{n+1}, y_{n+1}) makes it implicit in
+                          y_{n+1}, is applied m times, each pass evaluating f at
+                          the previous pass's value (not in the paper; a common
+                          variant of the predictor-corrector).  Forward solves
+                          only: abm_adjoint returns ABM_ERR_UNSUPPORTED for m > 1;
+                          YP still receives the predictor                      */
+  int reserved[6];     /* must be zero                                            */
 } abm_plan_opts;
 
 /* Fills *o with the defaults (FP64, n_max = 0, tile_B = 0 ...). */

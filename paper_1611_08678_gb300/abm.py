@@ -40,7 +40,8 @@ class PlanOpts(ctypes.Structure):
                 ("tile_B", ctypes.c_int), ("far_ctas", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("spin_timeout_cycles", ctypes.c_longlong), ("test_withhold_tile", ctypes.c_int),
                 ("profile", ctypes.c_int), ("near_warps", ctypes.c_int), ("far_split", ctypes.c_int),
-                ("near_split", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("near_split", ctypes.c_int), ("corrector_passes", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 _lib = None
@@ -138,7 +139,7 @@ class Plan:
     def __init__(self, system: str, n_max: int, max_batch: int = 0, prec: str = "fp64", tile_B: int = 0,
                  far_ctas: int = 0, use_graph: bool = False, spin_timeout_cycles: int = 0,
                  test_withhold_tile: int = 0, profile: bool = False, near_warps: int = 0,
-                 far_split: int = 0, near_split: int = 0):
+                 far_split: int = 0, near_split: int = 0, corrector_passes: int = 1):
         self.lib = load()
         self.system = system
         self.d = self.lib.abm_system_dim(SYSTEMS[system])
@@ -158,6 +159,7 @@ class Plan:
         o.near_warps = int(near_warps)
         o.far_split = int(far_split)
         o.near_split = int(near_split)
+        o.corrector_passes = int(corrector_passes)
         h = _vp()
         st = self.lib.abm_plan_create(ctypes.byref(h), SYSTEMS[system], ctypes.byref(o))
         if st != 0:

@@ -514,6 +514,7 @@ BatchArgs batch_args(abm_plan p, const Sched& S, const double* params, const dou
   A.YP = YP;
   A.ldY = ldY;
   A.status = p->status;
+  A.passes = p->o.corrector_passes > 1 ? p->o.corrector_passes : 1;
   return A;
 }
 
@@ -553,6 +554,7 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
   if (o->far_split < 0 || o->far_split > 64) return ABM_ERR_INVALID_ARG;
   if (o->near_split != 0 && o->near_split != 1 && o->near_split != 2 && o->near_split != 4 && o->near_split != 8)
     return ABM_ERR_INVALID_ARG;
+  if (o->corrector_passes < 0 || o->corrector_passes > 8) return ABM_ERR_INVALID_ARG;
   const bool tc_prec = o->prec == ABM_PREC_BF16X3_FAR || o->prec == ABM_PREC_BF16X6_FAR;
   if (tc_prec && (sys_dim(sys) != 3 || (o->tile_B && o->tile_B != 64))) return ABM_ERR_UNSUPPORTED;
   abm_plan p = new abm_plan_s();
@@ -760,6 +762,7 @@ abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* pa
   A.N = N;
   A.spin_budget = p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL;
   A.withhold_tile = p->o.test_withhold_tile > 0 ? p->o.test_withhold_tile - 1 : -1;
+  A.passes = p->o.corrector_passes > 1 ? p->o.corrector_passes : 1;
   {
     Trace tr(p, ABM_KERNEL_SINGLE, st);
     CK(launch_persistent(p->sys, A, p->Gp, st), "persistent single-trajectory kernel");
@@ -912,6 +915,8 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
     return fail(p, ABM_ERR_INVALID_ARG, "abm_adjoint: need 1 <= M <= max_batch and non-null arrays (Y and YP too)");
   if (p->o.prec == ABM_PREC_FP32_FAR)
     return fail(p, ABM_ERR_UNSUPPORTED, "abm_adjoint: FP64 or tensor-core (BF16X3/X6) plans only");
+  if (p->o.corrector_passes > 1)
+    return fail(p, ABM_ERR_UNSUPPORTED, "abm_adjoint: the adjoint of PECE only (corrector_passes <= 1)");
   cudaStream_t st = (cudaStream_t)stream;
   const int B = p->B, d = p->d;
   Sched S;

@@ -176,12 +176,24 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
 #pragma unroll
       for (int k = 0; k < D; ++k) ypv[k] = ysh[par][k][lane];
       const double fp = S::fc(c, p, alpha, t1, ypv);
-      const double y = fma(hh, fma(g, fp, sc), y0c);
+      double y = fma(hh, fma(g, fp, sc), y0c);
       ysh2[par][c][lane] = y;
       asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
       double yv[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) yv[k] = ysh2[par][k][lane];
+      // P(EC)^m E: further corrector passes evaluate f at the previous pass's
+      // state; the exchange alternates between ysh and ysh2 (every chain warp
+      // read the other one before the barrier it just passed)
+      for (int it = 1; it < A.passes; ++it) {
+        const double fq = S::fc(c, p, alpha, t1, yv);
+        y = fma(hh, fma(g, fq, sc), y0c);
+        double(*xb)[32] = (it & 1) ? ysh[par] : ysh2[par];
+        xb[c][lane] = y;
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
+#pragma unroll
+        for (int k = 0; k < D; ++k) yv[k] = xb[k][lane];
+      }
       const double fy = S::fc(c, p, alpha, t1, yv);
       Fw[i + 1][col] = fy;
       F[(n + 1) * ld + col] = fy;
@@ -355,12 +367,23 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
 #pragma unroll
     for (int k = 0; k < D; ++k) ypv[k] = ysh[par][k][j];
     const double fp = S::fc(c, p, alpha, t1, ypv);
-    const double y = fma(hh, fma(g, fp, sc), y0c);
+    double y = fma(hh, fma(g, fp, sc), y0c);
     if (l == 0) ysh2[par][c][j] = y;
     asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
     double yv[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) yv[k] = ysh2[par][k][j];
+    // P(EC)^m E passes, exchanged through ysh / ysh2 alternately as in
+    // batched_near_kernel
+    for (int it = 1; it < A.passes; ++it) {
+      const double fq = S::fc(c, p, alpha, t1, yv);
+      y = fma(hh, fma(g, fq, sc), y0c);
+      double(*xb)[T] = (it & 1) ? ysh[par] : ysh2[par];
+      if (l == 0) xb[c][j] = y;
+      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+#pragma unroll
+      for (int k = 0; k < D; ++k) yv[k] = xb[k][j];
+    }
     const double fy = S::fc(c, p, alpha, t1, yv);
     if (l == 0) {
       Fw[i + 1][cloc] = fy;

@@ -53,6 +53,7 @@ struct BatchArgs {
   double* YP;
   long long ldY;
   unsigned long long* status;
+  int passes;              // corrector passes per step (1 = PECE)
 };
 
 // Arguments of the tensor-core far kernel (far_tc.cu).

@@ -36,6 +36,7 @@ struct PersistArgs {
   int N;
   long long spin_budget;       // clock64 cycles per wait
   int withhold_tile;           // testing: far CTAs never count this tile (-1 = off)
+  int passes;                  // corrector passes per step (1 = PECE)
 };
 
 cudaError_t launch_far_single(int d, const FarSingleArgs& A, int B, int grid, cudaStream_t st);

@@ -261,12 +261,24 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
 #pragma unroll
           for (int q = 0; q < D; ++q) ypv[q] = ysh[q];
           const double fp = S::fc(c, p, A.alpha, t1, ypv);
-          const double y = fma(hh, fma(g, fp, vc), y0c);
+          double y = fma(hh, fma(g, fp, vc), y0c);
           if (lane == 0) ysh2[c] = y;
           named_bar(2, 32 * D);
           double yv[D];
 #pragma unroll
           for (int q = 0; q < D; ++q) yv[q] = ysh2[q];
+          // P(EC)^m E: further corrector passes evaluate f at the previous
+          // pass's state; the exchange alternates between ysh and ysh2 (every
+          // warp read the other one before the barrier it just passed)
+          for (int it = 1; it < A.passes; ++it) {
+            const double fq = S::fc(c, p, A.alpha, t1, yv);
+            y = fma(hh, fma(g, fq, vc), y0c);
+            double* xb = (it & 1) ? ysh : ysh2;
+            if (lane == 0) xb[c] = y;
+            named_bar(2, 32 * D);
+#pragma unroll
+            for (int q = 0; q < D; ++q) yv[q] = xb[q];
+          }
           const double fy = S::fc(c, p, A.alpha, t1, yv);
           if (lane == 0) {
             Fs[(n + 1) & 3][c] = fy;
@@ -477,6 +489,7 @@ extern "C" abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, 
   A.N = N;
   A.spin_budget = 4000000000LL;
   A.withhold_tile = -1;
+  A.passes = 1;
   if ((e = launch_persistent(sys, A, grid, st)) != cudaSuccess) return cuda_err(e, "persistent kernel");
   unsigned long long w = 0;
   if ((e = cudaMemcpyAsync(&w, A.status, sizeof(w), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
