@@ -6,8 +6,9 @@ arithmetic changes, so a change to the oracle is always a deliberate one.
 Regenerate with ``python tests/golden/make_oracle_snapshots.py``.
 
 Cases: the fractional ABM PECE scheme of Section 2 (eq. (2) predictor, product
-trapezoid corrector) on every built-in right-hand side, and the weights b_m,
-a_m, c_m, g of Section 2 at lags on both sides of the kernels' series switch.
+trapezoid corrector) on every built-in right-hand side, three P(EC)^m E solves
+(the corrector repeated m times per step), and the weights b_m, a_m, c_m, g of
+Section 2 at lags on both sides of the kernels' series switch.
 """
 import os
 import sys
@@ -28,6 +29,8 @@ SOLVES = [
     ("hindmarsh_rose", 0.98, 0.01, 64, [1.0, 3.0, 1.0, 5.0, 0.006, 4.0, -1.6, 3.25], [0.1, 0.2, 0.3]),
 ]
 SOLVE_ROWS = [1, 2, 3, 17, 33, 63, 64]
+# (case index into SOLVES, corrector passes m > 1): P(EC)^m E solves
+PECM = [(2, 2), (4, 3), (6, 2)]
 WEIGHT_ALPHAS = [0.3, 0.5, 0.9, 0.98, 1.0]
 WEIGHT_LAGS = [0, 1, 2, 15, 16, 17, 31, 32, 33, 1000, 65536, 262144]
 
@@ -40,6 +43,12 @@ def lines():
             for j in range(Y.shape[1]):
                 out.append(f"Y {i} {n} {j} {float(Y[n, j])!r}")
                 out.append(f"YP {i} {n} {j} {float(YP[n, j])!r}")
+    for q, (i, m) in enumerate(PECM):
+        system, alpha, h, N, p, y0 = SOLVES[i]
+        Y, _ = oracle.solve(system, alpha, h, N, p, y0, passes=m)
+        for n in SOLVE_ROWS:
+            for j in range(Y.shape[1]):
+                out.append(f"YM {q} {n} {j} {float(Y[n, j])!r}")
     for i, alpha in enumerate(WEIGHT_ALPHAS):
         b, a, c, g = oracle.weights(alpha, WEIGHT_LAGS[-1])
         for m in WEIGHT_LAGS:

@@ -57,7 +57,15 @@ def test_oracle_matches_snapshots(snapshot_generator):
     weights = {}
     for kind, case, idx, comp, val in stored:
         case, idx, comp, val = int(case), int(idx), int(comp), float(val)
-        if kind in ("Y", "YP"):
+        if kind == "YM":
+            key = ("m", case)
+            if key not in solves:
+                i, m = gen.PECM[case]
+                system, alpha, h, N, p, y0 = gen.SOLVES[i]
+                solves[key] = oracle.solve(system, alpha, h, N, p, y0, passes=m)[0]
+            Y = solves[key]
+            assert abs(Y[idx, comp] - val) <= 1e-13 * max(np.abs(Y).max(), 1e-300), (kind, case, idx, comp)
+        elif kind in ("Y", "YP"):
             if case not in solves:
                 system, alpha, h, N, p, y0 = gen.SOLVES[case]
                 solves[case] = oracle.solve(system, alpha, h, N, p, y0)
