@@ -21,8 +21,10 @@ Parity status per function (each pin lives in ``tests/test_oracle.py``):
                corrector's solution, solved in closed form step by step;
                y-independent forcing gives the same result for every m.
   tangent      pinned: central finite differences of ``solve``.
-  history      pinned: brute-force Python double loop on tiny inputs and the
-               identity that it reproduces the sums inside ``solve``.
+  history      pinned through the pinned solve: its predictor sum gives every
+               y^P_{n+1} and its corrector sum (c_n at row 0, a_{n-k} beyond)
+               every y_{n+1} of a solve; row ranges split and add up; three
+               compiled mutants of it are rejected.
 """
 from __future__ import annotations
 

@@ -370,6 +370,12 @@ def test_lorenz_divergence_is_constant():
 # History sums and the tangent-linear gradient.
 # ---------------------------------------------------------------------------
 def test_history_brute_force_and_solve_identity():
+    """oracle_history is pinned through the pinned solve: its predictor sum P
+    reproduces y^P_{n+1} = y0 + h^a P (eq. 2) and its corrector sum C (c_n at
+    k = 0, a_{n-k} for k >= 1) reproduces y_{n+1} = y0 + h^a (C + g f(t_{n+1},
+    y^P_{n+1})) (the corrector of Sec. 2) for every step of a Lorenz solve;
+    a split of the row range [k_lo, k_hi) adds up to the whole range, with the
+    c_n weight tied to row 0, not to the first row of a range."""
     rng = np.random.default_rng(1611)
     alpha, n = 0.73, 17
     b, a, c, g = oracle.weights(alpha, n + 1)
@@ -379,13 +385,20 @@ def test_history_brute_force_and_solve_identity():
         sp = sum(b[n - k] * F[k, col] for k in range(n + 1))
         sc = c[n] * F[0, col] + sum(a[n - k] * F[k, col] for k in range(1, n + 1))
         assert abs(P[col] - sp) < 1e-14 * (1 + abs(sp)) and abs(C[col] - sc) < 1e-14 * (1 + abs(sc))
-    # the solve's own predictor equals y0 + h^a * history sum
-    h = 0.01
-    Y, YP, Fs = oracle.solve("lorenz", alpha, h, 40, [10.0, 28.0, 8 / 3], [0.1, 0.2, 0.3], return_f=True)
+    for m in (1, 5, n):
+        P0, C0 = oracle.history(b, a, c, F, n, 0, m)
+        P1, C1 = oracle.history(b, a, c, F, n, m, n + 1)
+        np.testing.assert_allclose(P0 + P1, P, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(C0 + C1, C, rtol=1e-13, atol=1e-13)
+    # the solve's own predictor and corrector equal y0 + h^a * history sums
+    h, p, y0 = 0.01, [10.0, 28.0, 8 / 3], np.array([0.1, 0.2, 0.3])
+    Y, YP, Fs = oracle.solve("lorenz", alpha, h, 40, p, y0, return_f=True)
     b, a, c, g = oracle.weights(alpha, 40)
-    for nn in (0, 5, 39):
+    for nn in range(40):
         P, C = oracle.history(b, a, c, Fs, nn, 0, nn + 1)
-        np.testing.assert_allclose(YP[nn + 1], np.array([0.1, 0.2, 0.3]) + h ** alpha * P, rtol=1e-14)
+        np.testing.assert_allclose(YP[nn + 1], y0 + h ** alpha * P, rtol=1e-14)
+        fP = oracle.rhs("lorenz", alpha, p, (nn + 1) * h, YP[nn + 1])
+        np.testing.assert_allclose(Y[nn + 1], y0 + h ** alpha * (C + g * fP), rtol=1e-14)
 
 
 @pytest.mark.parametrize("system,p,y0,alpha,h,N", [
@@ -443,6 +456,12 @@ MUTANTS = {
     # P(EC)^m E: one pass short, and every pass evaluated at the predictor
     "pecm_pass_count": ("for (int j = 1; j <= m; ++j) {", "for (int j = 1; j < m; ++j) {"),
     "pecm_stale_state": ("oracle_rhs(sys, alpha, p, tn1, yj, fj);", "oracle_rhs(sys, alpha, p, tn1, yp, fj);"),
+    # history sums of one target (the quantity the GPU far/near kernels split)
+    "history_corrector_lag_shift": ("sc += ((k == 0) ? c[n] : a[n - k]) * fk;",
+                                    "sc += ((k == 0) ? c[n] : a[n - k + 1]) * fk;"),
+    "history_c_weight_at_range_start": ("sc += ((k == 0) ? c[n] : a[n - k]) * fk;",
+                                        "sc += ((k == k_lo) ? c[n] : a[n - k]) * fk;"),
+    "history_predictor_lag_shift": ("sp += b[n - k] * fk;", "sp += b[n - k + 1] * fk;"),
 }
 
 
@@ -457,6 +476,7 @@ def _pins_pass():
         lambda: test_mittag_leffler(0.9, -1.0),
         test_lorenz_divergence_is_constant,
         lambda: test_pecm_matches_closed_form_passes(0.6, 0.05, -2.0, 3),
+        test_history_brute_force_and_solve_identity,
     ] + [lambda e=e: test_rhs_vanishes_at_equilibria(*e) for e in _equilibria()]
     for chk in checks:
         try:
