@@ -157,8 +157,15 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
 abm_status abm_plan_destroy(abm_plan p);
 
 /* Synchronises `stream`, then returns and clears the plan's device status
- * word (ABM_OK, ABM_ERR_NONFINITE or ABM_ERR_TIMEOUT).  If `where` is not
- * NULL it receives the packed detail (trajectory index << 32 | step). */
+ * word (ABM_OK, ABM_ERR_NONFINITE or ABM_ERR_TIMEOUT); abm_last_error() then
+ * names where it happened.  If `where` is not NULL it receives the packed
+ * detail: for ABM_ERR_NONFINITE trajectory << 32 | step of the first
+ * non-finite value; for ABM_ERR_TIMEOUT site << 56 | unit << 32 | position,
+ * site 1 = the single-trajectory stepping CTA waiting for the far sums of
+ * time tile `unit`, 2 = a single-trajectory far CTA waiting for the rows
+ * before time tile `unit`, 3..5 = the tensor-core far kernel of column tile
+ * `unit` (3 loader, 4 MMA issuer waiting for an accumulator, 5 MMA issuer
+ * waiting for the operands of K block `position`). */
 abm_status abm_plan_sync(abm_plan p, void* stream, int64_t* where);
 
 /* Message of the last failure on this plan (owned by the plan, valid until
@@ -278,9 +285,11 @@ abm_status abm_plan_kernel_times(abm_plan p, abm_kernel_kind kind, void* stream,
  * NULL), plus errbuf/errbuf_len (may be NULL/0): a message for any failure,
  * the empty string on success.
  *
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  The call is synchronous: it waits for `stream` and returns the
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing once the library's module is
+ * loaded; nothing is cached, so the address cannot go stale after a device
+ * reset).  The first call on a device may load that module: make it before
+ * any stream capture.  The call is synchronous: it waits for `stream` and returns the
  * device status (ABM_ERR_NONFINITE, ABM_ERR_TIMEOUT) itself.  All calls share
  * the one array, which keeps the previous call's contents (each call clears
  * what must start at zero), so calls that overlap on the GPU - from several

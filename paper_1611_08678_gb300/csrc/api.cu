@@ -13,6 +13,7 @@
 #include "batched.cuh"
 #include "common.cuh"
 #include "single.cuh"
+#include "status_text.h"
 
 namespace abm {
 // kernels (weights.cu, single.cu, batched.cu)
@@ -677,11 +678,9 @@ abm_status abm_plan_sync(abm_plan p, void* stream, int64_t* where) {
   int code = (int)(w >> 60);
   if (where) *where = (int64_t)(w & 0x0FFFFFFFFFFFFFFFull);
   if (code == 0) return ABM_OK;
-  char buf[160];
-  std::snprintf(buf, sizeof buf, "device reported %s at trajectory %llu step %llu",
-                code == ABM_ERR_NONFINITE ? "a non-finite value" : "a wait that ran out",
-                (w >> 32) & 0x0FFFFFFFull, w & 0xFFFFFFFFull);
-  return fail(p, (abm_status)code, buf);
+  char buf[200];
+  status_text(w, buf, sizeof buf);
+  return fail(p, (abm_status)code, std::string("device reported ") + buf);
 }
 
 abm_status abm_weights(abm_plan p, double alpha, int M, double* b, double* a, double* c, void* stream) {

@@ -21,6 +21,24 @@ __device__ __forceinline__ void report_status(unsigned long long* status, int co
   atomicCAS(status, 0ull, w);
 }
 
+// Sites of a bounded wait that ran out (bits 56..59 of an ABM_ERR_TIMEOUT
+// status word; bits 32..55 hold the index of the unit that waited, bits 0..31
+// a position inside it).
+enum TimeoutSite : int {
+  kSiteSingleNear = 1,    // single trajectory: stepping CTA waiting for tile `index`'s far sums
+  kSiteSingleFar = 2,     // single trajectory: far CTA waiting for the rows before tile `index`
+  kSiteFarProducer = 3,   // tensor-core far kernel, column tile `index`: loader after `pos` loads
+  kSiteFarAccum = 4,      // ... MMA issuer waiting for accumulator chunk `pos` to drain
+  kSiteFarLoad = 5        // ... MMA issuer waiting for the operands of K block `pos`
+};
+
+__device__ __forceinline__ void report_timeout(unsigned long long* status, int site, long long index,
+                                               long long pos) {
+  unsigned long long w = ((unsigned long long)ABM_ERR_TIMEOUT << 60) | ((unsigned long long)(site & 0xF) << 56) |
+                         (((unsigned long long)index & 0xFFFFFFull) << 32) | ((unsigned long long)pos & 0xFFFFFFFFull);
+  atomicCAS(status, 0ull, w);
+}
+
 // x is neither infinite nor NaN: an exponent-bit test on the integer pipe
 // (GB300's FP64 pipe is the bottleneck of the sequential steps).
 __device__ __forceinline__ bool finite_bits(double x) {

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
       }
       if (!ok) {
         abort_flag = 1;
-        report_status(A.status, ABM_ERR_TIMEOUT, tile, 1000 + nw);
+        report_timeout(A.status, kSiteFarProducer, tile, nw);
         // wait (bounded) for the loads already issued before giving up
         for (int j = max(0, nf - FST); j < nf; ++j) tc::mbar_wait(&ffull[j % FST], (j / FST) & 1, A.budget, nullptr);
         for (int j = max(0, nw - WST); j < nw; ++j) tc::mbar_wait(&wfull[j % WST], (j / WST) & 1, A.budget, nullptr);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
         const int buf = c % NBUF, use = c / NBUF;
         if (use >= 1 && !tc::mbar_wait(&acc_empty[buf], (use - 1) & 1, A.budget, &abort_flag)) {
           abort_flag = 1;
-          report_status(A.status, ABM_ERR_TIMEOUT, tile, 2000 + c);
+          report_timeout(A.status, kSiteFarAccum, tile, c);
           break;
         }
         tc::fence_after_sync();
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
           if (!tc::mbar_wait(&ffull[fs], (i / FST) & 1, A.budget, &abort_flag) ||
               !tc::mbar_wait(&wfull[ws], (i / WST) & 1, A.budget, &abort_flag)) {
             abort_flag = 1;
-            report_status(A.status, ABM_ERR_TIMEOUT, tile, 3000 + i);
+            report_timeout(A.status, kSiteFarLoad, tile, i);
             break;
           }
           tc::fence_after_sync();

@@ -27,10 +27,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "common.cuh"
 #include "single.cuh"
+#include "status_text.h"
 #include "systems.cuh"
 
 namespace abm {
@@ -44,13 +44,13 @@ constexpr int PT = 256;        // threads per CTA
 using dev_atomic = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
 
 __device__ bool spin_geq(unsigned long long* flag, unsigned long long target, unsigned long long* status,
-                         long long budget, int where, long long detail) {
+                         long long budget, int site, long long tile) {
   dev_atomic f(*flag), st(*status);
   const long long t0 = clock64();
   while (f.load(cuda::memory_order_acquire) < target) {
     if (st.load(cuda::memory_order_relaxed) != 0ull) return false;
     if (clock64() - t0 > budget) {
-      report_status(status, ABM_ERR_TIMEOUT, where, detail);
+      report_timeout(status, site, tile, 0);
       return false;
     }
     __nanosleep(64);
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
     const int w = blockIdx.x - 1;
     for (int j = 2; j < ntiles; ++j) {
       const long long s = (long long)j * PB, e = (long long)(j - 1) * PB;
-      if (tid == 0) ok_s = spin_geq(rows_done, (unsigned long long)e, A.status, A.spin_budget, 1, j);
+      if (tid == 0) ok_s = spin_geq(rows_done, (unsigned long long)e, A.status, A.spin_budget, kSiteSingleFar, j);
       __syncthreads();
       if (!ok_s) return;
       const long long K = e - 1, chunk = (K + W - 1) / W;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
     if (j >= 2) {
       if (tid == 0) {
         const unsigned long long target = (unsigned long long)W * (unsigned long long)((j - 2) / PR + 1);
-        ok_s = spin_geq(far_count + (j % PR), target, A.status, A.spin_budget, 0, j);
+        ok_s = spin_geq(far_count + (j % PR), target, A.status, A.spin_budget, kSiteSingleNear, j);
       }
       __syncthreads();
       if (!ok_s) return;
@@ -388,9 +388,6 @@ constexpr size_t kScratchDoubles = kOffFlags + kAlignD;  // flags [0..4], status
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal
-
 void set_msg(char* buf, size_t len, const char* msg) {
   if (buf && len) std::snprintf(buf, len, "%s", msg);
 }
@@ -432,26 +429,25 @@ extern "C" abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, 
     tp.y0[i] = y0[i];
   }
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
     set_msg(errbuf, errbuf_len, "abm_solve_noalloc: no usable current device");
     return ABM_ERR_CUDA;
   }
+  // the array's device address on the current device, looked up on every call
+  // (this allocates nothing once the library's module is loaded; the first
+  // call on a device may load it); never cached, so it cannot go stale after
+  // a device reset
   double* base = nullptr;
   {
-    // once per device, with that device current: the array's device address
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-      void* ptr = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        char m[160];
-        std::snprintf(m, sizeof m, "abm_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-        set_msg(errbuf, errbuf_len, m);
-        return ABM_ERR_CUDA;
-      }
-      g_noalloc_ptr[dev] = (double*)ptr;
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      char m[160];
+      std::snprintf(m, sizeof m, "abm_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      set_msg(errbuf, errbuf_len, m);
+      return ABM_ERR_CUDA;
     }
-    base = g_noalloc_ptr[dev];
+    base = (double*)ptr;
   }
   int grid = persistent_max_grid(sys);
   int sms = 0;
@@ -469,7 +465,8 @@ extern "C" abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, 
   double* flags_d = base + kOffFlags;  // [0..4] wait flags, [8] status word
   // flags and status must start at zero: the array keeps the last call's contents
   if ((e = cudaMemsetAsync(flags_d, 0, kAlignD * sizeof(double), st)) != cudaSuccess) return cuda_err(e, "memset");
-  if ((e = launch_weights(alpha, (int)kWeightLen - 1, base + kOffB, base + kOffA, base + kOffC, base + kOffG, st)) !=
+  // lags 0..N+2B+1: the largest lag the kernel reads is below N + 2B
+  if ((e = launch_weights(alpha, N + 2 * kPersistB + 1, base + kOffB, base + kOffA, base + kOffC, base + kOffG, st)) !=
       cudaSuccess)
     return cuda_err(e, "weights kernel");
   PersistArgs A{};
@@ -497,9 +494,9 @@ extern "C" abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, 
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_err(e, "stream synchronize");
   const int code = (int)(w >> 60);
   if (code) {
-    char m[160];
-    std::snprintf(m, sizeof m, "abm_solve_noalloc: device reported %s at step %llu",
-                  code == ABM_ERR_NONFINITE ? "a non-finite value" : "a wait that ran out", w & 0xFFFFFFFFull);
+    char t[200], m[240];
+    status_text(w, t, sizeof t);
+    std::snprintf(m, sizeof m, "abm_solve_noalloc: device reported %s", t);
     set_msg(errbuf, errbuf_len, m);
     return (abm_status)code;
   }

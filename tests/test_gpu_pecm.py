@@ -59,6 +59,29 @@ def test_batched_pecm_matches_oracle(abm, near_split, prec, tol):
     assert worst <= tol, (near_split, prec, worst)
 
 
+def test_pecm_top_of_range_ragged_tiles(abm):
+    """m = 8, the largest accepted pass count, with N = 777 (not a multiple of
+    the 32-step or 64-step time tiles), so the ysh/ysh2 exchange alternates
+    through every parity across tile boundaries: persistent single-trajectory
+    kernel and the batched split near kernel (8 CTAs per tile)."""
+    p, y0 = [10.0, 28.0, 8.0 / 3.0], [0.1, 0.1, 0.1]
+    Yo, YPo = oracle.solve("lorenz", 0.98, 0.01, 777, p, y0, passes=8)
+    plan = abm.Plan("lorenz", n_max=777, corrector_passes=8)
+    Y, YP = plan.solve(0.98, 0.01, 777, p, y0, want_yp=True)
+    assert rel_err(Y.cpu().numpy()[:501], Yo[:501]) <= 1e-11
+    assert rel_err(YP.cpu().numpy()[1:501], YPo[1:501]) <= 1e-11
+    M = 40
+    bplan = abm.Plan("lorenz", n_max=777, max_batch=M, near_split=8, corrector_passes=8)
+    al, hh, NN = np.full(M, 0.98), np.full(M, 0.01), np.full(M, 777)
+    rng = np.random.default_rng(1611)
+    P = np.tile(p, (M, 1)) + rng.normal(0.0, 0.05, (M, 3))
+    Y0 = np.tile(y0, (M, 1))
+    Yb = bplan.solve_batched(al, hh, NN, P, Y0).cpu().numpy()
+    for i in (0, 17, M - 1):
+        Yi, _ = oracle.solve("lorenz", 0.98, 0.01, 500, P[i], Y0[i], passes=8)
+        assert rel_err(Yb[i, :501], Yi) <= 1e-11, i
+
+
 def test_adjoint_rejects_pecm_plans(abm):
     batch = workloads.random_batch("lorenz", 4, 50, 80, [0.9])
     plan = abm.Plan("lorenz", n_max=80, max_batch=4, corrector_passes=2)
