@@ -20,6 +20,13 @@ Parity status per function (each pin lives in ``tests/test_oracle.py``):
                pinned: on D^a y = lam y many passes reach the implicit
                corrector's solution, solved in closed form step by step;
                y-independent forcing gives the same result for every m.
+  solve_ext    (orders in (0, 2], one per component, y'(0) in the Taylor sum)
+               pinned: equal to ``solve`` operation for operation when the
+               orders agree and are at most one; exact for y-independent
+               linear forcing at orders above one; the alpha = 2 weights in
+               closed form and order 2 on y'' = -y; Mittag-Leffler
+               y0 E_a(lam t^a) + y1 t E_{a,2}(lam t^a); a decoupled Lorenz
+               case whose components equal scalar solves at their own orders.
   tangent      pinned: central finite differences of ``solve``.
   history      pinned through the pinned solve: its predictor sum gives every
                y^P_{n+1} and its corrector sum (c_n at row 0, a_{n-k} beyond)
@@ -80,6 +87,8 @@ def _bind(lib):
     lib.oracle_tangent.restype = I
     lib.oracle_solve_pecm.argtypes = [I, D, D, L, _dp, _dp, I, _dp, _dp, _dp]
     lib.oracle_solve_pecm.restype = I
+    lib.oracle_solve_ext.argtypes = [I, _dp, _dp, D, L, _dp, _dp, I, _dp, _dp, _dp]
+    lib.oracle_solve_ext.restype = I
     return lib
 
 
@@ -212,6 +221,26 @@ def solve(system: str, alpha: float, h: float, N: int, params, y0, return_f: boo
                                        int(passes), _ptr(Y), _ptr(YP), _ptr(F) if return_f else None)
     if rc:
         raise ValueError(f"oracle_solve failed (rc={rc})")
+    return (Y, YP, F) if return_f else (Y, YP)
+
+
+def solve_ext(system: str, alpha, h: float, N: int, params, y0, y0d=None, passes: int = 1,
+              return_f: bool = False):
+    """The general problem of eq. (1) (oracle_solve_ext): alpha a scalar or
+    one order per component, each in (0, 2]; y0d the initial derivatives
+    y'(0) (used where alpha > 1; None = zero).  Returns (Y, YP[, F])."""
+    d = dim(system)
+    al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (d,)))
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    y0a = np.ascontiguousarray(y0, dtype=np.float64).reshape(d)
+    yd = None if y0d is None else np.ascontiguousarray(y0d, dtype=np.float64).reshape(d)
+    Y = np.empty((N + 1, d)); YP = np.empty((N + 1, d))
+    F = np.empty((N + 1, d)) if return_f else None
+    rc = _load().oracle_solve_ext(_sys_id(system), _ptr(al), _ptr(yd) if yd is not None else None, float(h),
+                                  int(N), _ptr(p), _ptr(y0a), int(passes), _ptr(Y), _ptr(YP),
+                                  _ptr(F) if return_f else None)
+    if rc:
+        raise ValueError(f"oracle_solve_ext failed (rc={rc})")
     return (Y, YP, F) if return_f else (Y, YP)
 
 

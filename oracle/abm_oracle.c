@@ -25,7 +25,10 @@
  *   - the printed b_n has a '+' between the two powers; it is read as '-',
  *     the product-rectangle weight (the '+' version does not reduce to the
  *     rectangle rule at alpha = 1 and is not the integral of the kernel);
- *   - alpha is restricted to (0, 1], so the Taylor sum of eq. (2) is y_0 alone;
+ *   - oracle_solve and oracle_solve_pecm take alpha in (0, 1], where the
+ *     Taylor sum of eq. (2) is y_0 alone; oracle_solve_ext takes the general
+ *     problem of eq. (1): alpha in (0, 2] with the initial derivative y'(0)
+ *     in the Taylor sum where ceil(alpha) = 2, and one order per component;
  *   - one corrector pass per step (PECE), F_k evaluated at the corrected y_k.
  * The weights are evaluated from the plain definitions in binary128
  * (__float128 on x86-64, long double on AArch64 Linux, both IEEE quad) and
@@ -193,7 +196,7 @@ void oracle_jac(int sys, double alpha, const double* p, double t, const double* 
 /* ---- weights (Sec. 2), binary128 from the plain definitions, rounded to FP64 ----
  * Fills b[m], a[m], c[m] for m = 0..M and *g = 1/Gamma(alpha+2). */
 int oracle_weights(double alpha, long M, double* b, double* a, double* c, double* g) {
-  if (!(alpha > 0.0 && alpha <= 1.0) || M < 0) return 1;
+  if (!(alpha > 0.0 && alpha <= 2.0) || M < 0) return 1;
   qreal al = (qreal)alpha, one = 1;
   qreal ga1 = QGAMMA(al + one);      /* Gamma(alpha+1) */
   qreal ga2 = QGAMMA(al + 2 * one);  /* Gamma(alpha+2) */
@@ -229,6 +232,87 @@ void oracle_history(const double* b, const double* a, const double* c, long cols
     P[col] = sp;
     C[col] = sc;
   }
+}
+
+/* ---- the general problem of eq. (1): orders above one, one order per component ----
+ * Component i of D_*^{alpha_i} y_i = f_i(t, y) has its own order alpha_i in
+ * (0, 2] (a non-commensurate system when they differ), its own weights
+ * b^(i), a^(i), c^(i) (Sec. 2 definitions at alpha_i), h^{alpha_i} and
+ * 1/Gamma(alpha_i+2), and the Taylor sum of eq. (2) and of the corrector,
+ *   T_i(t) = sum_{k=0..ceil(alpha_i)-1} t^k / k! y_i^{(k)}(0),
+ * which for alpha_i in (1, 2] adds t y_i'(0) to y_i(0).  y0d holds the d
+ * initial derivatives y_i'(0) (NULL: all zero); they enter only components
+ * with alpha_i > 1.  m corrector passes per step (m = 1: PECE):
+ *   y^P_{n+1,i} = T_i(t_{n+1}) + h^{alpha_i} sum_{k=0..n} b^(i)_{n-k} F_{k,i}
+ *   y^(j)_i     = T_i(t_{n+1}) + h^{alpha_i} (c^(i)_n F_{0,i} + sum_{k=1..n} a^(i)_{n-k} F_{k,i}
+ *                                             + g_i f_i(t_{n+1}, y^(j-1))),  y^(0) = y^P
+ *   y_{n+1} = y^(m),  F_{n+1} = f(t_{n+1}, y_{n+1}).
+ * With every alpha_i equal and in (0, 1] this is oracle_solve (m = 1) or
+ * oracle_solve_pecm, operation for operation.  The system's own use of alpha
+ * (the manufactured right-hand side) takes alpha_0. */
+int oracle_solve_ext(int sys, const double* alpha, const double* y0d, double h, long N, const double* p,
+                     const double* y0, int m, double* Y, double* YP, double* Fout) {
+  int d = oracle_dim(sys);
+  if (d < 1 || !(h > 0.0) || N < 1 || m < 1) return 1;
+  for (int i = 0; i < d; ++i)
+    if (!(alpha[i] > 0.0 && alpha[i] <= 2.0)) return 1;
+  double *wb[3] = {0}, *wa[3] = {0}, *wc[3] = {0};
+  double g[3], hat[3];
+  int ceil_a[3];
+  double* F = Fout ? Fout : malloc(sizeof(double) * (N + 1) * d);
+  int bad = !F;
+  for (int i = 0; i < d && !bad; ++i) {
+    wb[i] = malloc(sizeof(double) * (N + 1));
+    wa[i] = malloc(sizeof(double) * (N + 1));
+    wc[i] = malloc(sizeof(double) * (N + 1));
+    bad = !wb[i] || !wa[i] || !wc[i];
+    if (!bad) oracle_weights(alpha[i], N, wb[i], wa[i], wc[i], &g[i]);
+    hat[i] = pow(h, alpha[i]);
+    ceil_a[i] = alpha[i] > 1.0 ? 2 : 1;
+  }
+  if (bad) {
+    for (int i = 0; i < d; ++i) { free(wb[i]); free(wa[i]); free(wc[i]); }
+    if (!Fout) free(F);
+    return 2;
+  }
+  double yp[3], yj[3], fj[3], sc[3], taylor[3];
+  for (int i = 0; i < d; ++i) { Y[i] = y0[i]; YP[i] = y0[i]; }
+  oracle_rhs(sys, alpha[0], p, 0.0, y0, F);
+  for (long n = 0; n < N; ++n) {
+    double tn1 = (double)(n + 1) * h;
+    for (int i = 0; i < d; ++i) {             /* Taylor sum of the initial values */
+      double term = y0[i], tk = 1.0;
+      taylor[i] = 0.0;
+      for (int k = 0; k < ceil_a[i]; ++k) {
+        taylor[i] += term;
+        tk *= tn1;
+        term = (y0d ? y0d[i] : 0.0) * tk;     /* k = 1: t y'(0) (1! = 1) */
+      }
+    }
+    for (int i = 0; i < d; ++i) {             /* predictor, eq. (2), component i's weights */
+      double sum = 0.0;
+      for (long k = 0; k <= n; ++k) sum += wb[i][n - k] * F[k * d + i];
+      yp[i] = taylor[i] + hat[i] * sum;
+      yj[i] = yp[i];
+    }
+    for (int i = 0; i < d; ++i) {             /* corrector history part */
+      double sum = wc[i][n] * F[i];
+      for (long k = 1; k <= n; ++k) sum += wa[i][n - k] * F[k * d + i];
+      sc[i] = sum;
+    }
+    for (int pass = 1; pass <= m; ++pass) {   /* m corrector passes */
+      oracle_rhs(sys, alpha[0], p, tn1, yj, fj);
+      for (int i = 0; i < d; ++i) yj[i] = taylor[i] + hat[i] * (sc[i] + g[i] * fj[i]);
+    }
+    for (int i = 0; i < d; ++i) {
+      Y[(n + 1) * d + i] = yj[i];
+      YP[(n + 1) * d + i] = yp[i];
+    }
+    oracle_rhs(sys, alpha[0], p, tn1, Y + (n + 1) * d, F + (n + 1) * d);
+  }
+  for (int i = 0; i < d; ++i) { free(wb[i]); free(wa[i]); free(wc[i]); }
+  if (!Fout) free(F);
+  return 0;
 }
 
 /* ---- the ABM PECE solve (Sec. 2) ----

@@ -86,7 +86,7 @@ def test_weights_alpha_one_are_rectangle_and_trapezoid():
 
 
 def test_weights_reject_bad_alpha():
-    for al in (0.0, -0.5, 1.5, float("nan")):
+    for al in (0.0, -0.5, 2.5, float("nan")):
         with pytest.raises(ValueError):
             oracle.weights(al, 4)
 
@@ -288,6 +288,129 @@ def test_alpha_one_order_two_to_exponential():
 
 
 # ---------------------------------------------------------------------------
+# The general problem of eq. (1): orders in (1, 2] with y'(0) in the Taylor
+# sum of eq. (2) and the corrector, and one order per component.
+# ---------------------------------------------------------------------------
+def _mittag_leffler2(alpha, beta, z):
+    """E_{a,b}(z) = sum_k z^k / Gamma(a k + b), in 60-digit arithmetic."""
+    mp = mpmath.mp
+    mp.dps = 60
+    z = mp.mpf(z)
+    s, k = mp.mpf(0), 0
+    while True:
+        term = z ** k / mp.gamma(alpha * k + beta)
+        s += term
+        if k > 10 and abs(term) < mp.mpf(10) ** -40:
+            break
+        k += 1
+    return float(s)
+
+
+def test_ext_equals_solve_for_commensurate_orders():
+    """Equal orders in (0, 1]: the general routine is the plain scheme."""
+    p, y0 = [10.0, 28.0, 8.0 / 3.0], [0.1, 0.1, 0.1]
+    Y, YP = oracle.solve("lorenz", 0.9, 0.01, 300, p, y0)
+    Ye, YPe = oracle.solve_ext("lorenz", [0.9, 0.9, 0.9], 0.01, 300, p, y0, y0d=[5.0, -1.0, 2.0])
+    assert np.array_equal(Y, Ye) and np.array_equal(YP, YPe)
+    Y3, _ = oracle.solve("lorenz", 0.9, 0.01, 300, p, y0, passes=3)
+    Y3e, _ = oracle.solve_ext("lorenz", 0.9, 0.01, 300, p, y0, passes=3)
+    assert np.array_equal(Y3, Y3e)
+
+
+@pytest.mark.parametrize("alpha", [1.2, 1.5, 1.9, 2.0])
+@pytest.mark.parametrize("h", [0.1, 0.013])
+def test_ext_linear_forcing_is_exact_above_one(alpha, h):
+    """For alpha in (1, 2] the Caputo problem D^a y = q0 + q1 t with y(0) = y0,
+    y'(0) = y1 has y = y0 + y1 t + q0 t^a/Gamma(a+1) + q1 t^(a+1)/Gamma(a+2);
+    the product trapezoid reproduces it at every grid point, the product
+    rectangle whenever q1 = 0."""
+    N, q0, q1, y0, y1 = 300, 1.3, -0.7, 0.25, -0.6
+    Y, _ = oracle.solve_ext("linear", alpha, h, N, [0.0, q0, q1], [y0], y0d=[y1])
+    t = np.arange(N + 1) * h
+    ex = y0 + y1 * t + q0 * t ** alpha / math.gamma(alpha + 1) + q1 * t ** (alpha + 1) / math.gamma(alpha + 2)
+    tol = 8 * N * np.finfo(float).eps * np.abs(ex).max()
+    assert np.max(np.abs(Y[:, 0] - ex)) < tol
+    _, YP = oracle.solve_ext("linear", alpha, h, N, [0.0, q0, 0.0], [y0], y0d=[y1])
+    exc = y0 + y1 * t + q0 * t ** alpha / math.gamma(alpha + 1)
+    assert np.max(np.abs(YP[1:, 0] - exc[1:])) < 8 * N * np.finfo(float).eps * np.abs(exc).max()
+
+
+def test_weights_alpha_two_closed_form():
+    """At alpha = 2 the weights are polynomials in m: b_m = (2m+1)/2,
+    a_m = m+1, c_m = (3m+2)/6, g = 1/6 (Sec. 2 definitions by hand)."""
+    M = 5000
+    b, a, c, g = oracle.weights(2.0, M)
+    m = np.arange(M + 1)
+    assert np.array_equal(b, (2 * m + 1) / 2.0) and np.array_equal(a, m + 1.0)
+    ce = (3 * m + 2) / 6.0
+    assert np.all(np.abs(c - ce) <= np.spacing(ce))
+    assert g == 1.0 / 6.0
+
+
+@pytest.mark.parametrize("alpha", [1.3, 1.7])
+def test_weights_above_one_match_product_integration_quadrature(alpha):
+    n = 10
+    bq, aq, cq, gq = _quad_weights(alpha, n)
+    b, a, c, g = oracle.weights(alpha, n)
+    for m in range(n + 1):
+        assert abs(b[m] - float(bq[m])) <= 1e-14 * abs(float(bq[m])), (m, b[m], bq[m])
+    for m in range(n):
+        assert abs(a[m] - float(aq[m])) <= 1e-14 * abs(float(aq[m])), (m, a[m], aq[m])
+    assert abs(c[n] - float(cq)) <= 1e-14 * abs(float(cq))
+    assert abs(g - float(gq)) <= 1e-14 * abs(float(gq))
+
+
+@pytest.mark.parametrize("y1", [0.0, 1.0])
+def test_alpha_two_is_second_order_on_the_harmonic_oscillator(y1):
+    """alpha = 2: y'' = -y, y(0) = 1, y'(0) = y1 has y = cos t + y1 sin t; the
+    scheme (product rectangle / trapezoid of y = y0 + t y1 + int (t-s) f ds)
+    converges at order 2."""
+    errs = []
+    for h in [2.0 ** -5, 2.0 ** -6, 2.0 ** -7]:
+        N = int(round(2.0 / h))
+        Y, _ = oracle.solve_ext("linear", 2.0, h, N, [-1.0, 0.0, 0.0], [1.0], y0d=[y1])
+        t = np.arange(N + 1) * h
+        errs.append(np.max(np.abs(Y[:, 0] - (np.cos(t) + y1 * np.sin(t)))))
+    o1, o2 = math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])
+    assert abs(o1 - 2.0) < 0.15 and abs(o2 - 2.0) < 0.15, (o1, o2)
+
+
+@pytest.mark.parametrize("alpha", [1.3, 1.7])
+@pytest.mark.parametrize("lam", [-1.0, -2.0])
+def test_mittag_leffler_above_one(alpha, lam):
+    """D^a y = lam y, y(0) = y0, y'(0) = y1 (1 < a < 2) has
+    y = y0 E_a(lam t^a) + y1 t E_{a,2}(lam t^a); the error falls with h."""
+    T, y0, y1 = 2.0, 1.0, 0.5
+    ts = np.array([0.5, 1.0, 1.5, 2.0])
+    ex = np.array([y0 * _mittag_leffler2(alpha, 1.0, lam * t ** alpha)
+                   + y1 * t * _mittag_leffler2(alpha, 2.0, lam * t ** alpha) for t in ts])
+    errs = []
+    for h in [2.0 ** -5, 2.0 ** -7, 2.0 ** -9]:
+        N = int(round(T / h))
+        Y, _ = oracle.solve_ext("linear", alpha, h, N, [lam, 0.0, 0.0], [y0], y0d=[y1])
+        idx = np.rint(ts / h).astype(int)
+        errs.append(np.max(np.abs(Y[idx, 0] - ex) / np.maximum(np.abs(ex), 0.1)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-3
+
+
+def test_noncommensurate_orders_decouple():
+    """Lorenz with sigma = 0 and x(0) = 0 keeps x = 0, and then y and z obey
+    D^a y = -y and D^c z = -beta z on their own: with per-component orders
+    (0.8, 1.4, 0.6) every component equals the scalar solve at its own order
+    (bit for bit: the right-hand sides round identically)."""
+    beta = 8.0 / 3.0
+    al, y0, y0d = [0.8, 1.4, 0.6], [0.0, 0.7, -0.4], [0.0, 0.3, 0.0]
+    h, N = 0.01, 400
+    Y, YP = oracle.solve_ext("lorenz", al, h, N, [0.0, 28.0, beta], y0, y0d=y0d)
+    assert np.all(Y[:, 0] == 0.0)
+    Yy, YPy = oracle.solve_ext("linear", al[1], h, N, [-1.0, 0.0, 0.0], [y0[1]], y0d=[y0d[1]])
+    Yz, YPz = oracle.solve_ext("linear", al[2], h, N, [-beta, 0.0, 0.0], [y0[2]])
+    assert np.array_equal(Y[:, 1], Yy[:, 0]) and np.array_equal(YP[:, 1], YPy[:, 0])
+    assert np.array_equal(Y[:, 2], Yz[:, 0]) and np.array_equal(YP[:, 2], YPz[:, 0])
+
+
+# ---------------------------------------------------------------------------
 # Right-hand sides of the workload systems: equilibria, Jacobian consistency,
 # and the Lorenz flow's constant divergence -(sigma + 1 + beta).
 # ---------------------------------------------------------------------------
@@ -456,6 +579,13 @@ MUTANTS = {
     # P(EC)^m E: one pass short, and every pass evaluated at the predictor
     "pecm_pass_count": ("for (int j = 1; j <= m; ++j) {", "for (int j = 1; j < m; ++j) {"),
     "pecm_stale_state": ("oracle_rhs(sys, alpha, p, tn1, yj, fj);", "oracle_rhs(sys, alpha, p, tn1, yp, fj);"),
+    # the general problem: Taylor term, per-component weights, h^alpha and g
+    "ext_taylor_dropped": ("term = (y0d ? y0d[i] : 0.0) * tk;", "term = 0.0 * tk;"),
+    "ext_ceiling_one": ("ceil_a[i] = alpha[i] > 1.0 ? 2 : 1;", "ceil_a[i] = 1;"),
+    "ext_predictor_weights_shared": ("sum += wb[i][n - k] * F[k * d + i];", "sum += wb[0][n - k] * F[k * d + i];"),
+    "ext_corrector_weights_shared": ("sum += wa[i][n - k] * F[k * d + i];", "sum += wa[0][n - k] * F[k * d + i];"),
+    "ext_hhat_shared": ("hat[i] = pow(h, alpha[i]);", "hat[i] = pow(h, alpha[0]);"),
+    "ext_g_shared": ("taylor[i] + hat[i] * (sc[i] + g[i] * fj[i]);", "taylor[i] + hat[i] * (sc[i] + g[0] * fj[i]);"),
     # history sums of one target (the quantity the GPU far/near kernels split)
     "history_corrector_lag_shift": ("sc += ((k == 0) ? c[n] : a[n - k]) * fk;",
                                     "sc += ((k == 0) ? c[n] : a[n - k + 1]) * fk;"),
@@ -477,6 +607,9 @@ def _pins_pass():
         test_lorenz_divergence_is_constant,
         lambda: test_pecm_matches_closed_form_passes(0.6, 0.05, -2.0, 3),
         test_history_brute_force_and_solve_identity,
+        lambda: test_ext_linear_forcing_is_exact_above_one(1.5, 0.1),
+        test_noncommensurate_orders_decouple,
+        lambda: test_alpha_two_is_second_order_on_the_harmonic_oscillator(1.0),
     ] + [lambda e=e: test_rhs_vanishes_at_equilibria(*e) for e in _equilibria()]
     for chk in checks:
         try:
