@@ -177,7 +177,7 @@ const char* abm_last_error(abm_plan p);
  * Writes b[m], a[m], c[m] for m = 0..M (device arrays of M+1 doubles) for
  * this alpha in FP64.  Large lags use cancellation-free series, small lags a
  * 16-point Gauss-Legendre quadrature of the product-integration kernels.
- * alpha in (0, 1], M >= 0. */
+ * alpha in (0, 2] (the definitions hold for every positive order), M >= 0. */
 abm_status abm_weights(abm_plan p, double alpha, int M, double* b, double* a, double* c,
                        void* stream);
 
@@ -192,6 +192,19 @@ abm_status abm_weights(abm_plan p, double alpha, int M, double* b, double* a, do
 abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* params,
                      const double* y0, double* Y, double* YP, void* stream);
 
+/* The general problem of eq. (1) for one trajectory: an order per state
+ * component, each in (0, 2] (a non-commensurate system when they differ), and
+ * for components of order above one the initial derivative y_i'(0), which
+ * enters the Taylor sum of the predictor (eq. (2)) and of the corrector,
+ *     sum_{k=0..ceil(alpha_i)-1} t_{n+1}^k / k! y_i^(k)(0) = y_i(0) + t_{n+1} y_i'(0);
+ * component i uses the Sec. 2 weights b, a, c and h^alpha_i, 1/Gamma(alpha_i+2)
+ * of its own order.  alpha: host array of d orders; y0d: host array of d
+ * values or NULL (zero), read only for components with alpha_i > 1; every
+ * other argument as abm_solve.  ABM_ERR_INVALID_ARG for an order outside
+ * (0, 2] or a non-finite y0d. */
+abm_status abm_solve_ext(abm_plan p, const double* alpha, double h, int N, const double* params,
+                         const double* y0, const double* y0d, double* Y, double* YP, void* stream);
+
 /* Batched trajectories (independent problems with their own alpha, h, N,
  * parameters and initial values).  alpha, h, N: HOST arrays of M entries
  * (they drive the scheduling: trajectories are grouped by alpha and ordered
@@ -203,6 +216,20 @@ abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* pa
 abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const double* h,
                              const int* N, const double* params, const double* y0, double* Y,
                              long long ldY, double* YP, void* stream);
+
+/* The general problem of eq. (1) for a batch (see abm_solve_ext): alpha is a
+ * HOST array of M x d orders, each in (0, 2]; y0d a DEVICE array M x d of
+ * initial derivatives or NULL (zero), read for components of order above
+ * one; every other argument as abm_solve_batched.  Trajectories with equal
+ * order tuples share one weight set per component.  A batch may hold at most
+ * 24 distinct orders and 24 distinct order tuples (ABM_ERR_UNSUPPORTED
+ * beyond).  The tensor-core precisions (BF16X3/X6) take orders that are equal
+ * across the components of each trajectory (one Toeplitz operand per column
+ * tile) and return ABM_ERR_UNSUPPORTED otherwise; FP64 and FP32 plans take
+ * any orders. */
+abm_status abm_solve_batched_ext(abm_plan p, int M, const double* alpha, const double* h, const int* N,
+                                 const double* params, const double* y0, const double* y0d, double* Y,
+                                 long long ldY, double* YP, void* stream);
 
 /* abm_solve_batched with HOST buffers (the paper has no counterpart: it is
  * the call a user makes with inputs and results in host memory).  alpha, h,

@@ -25,7 +25,7 @@ STATUS = {0: "ABM_OK", 1: "ABM_ERR_INVALID_ARG", 2: "ABM_ERR_CUDA", 3: "ABM_ERR_
 EXPORTS = ["abm_plan_opts_default", "abm_system_dim", "abm_system_nparams", "abm_plan_create",
            "abm_plan_destroy", "abm_plan_sync", "abm_last_error", "abm_weights", "abm_solve",
            "abm_solve_batched", "abm_solve_batched_host", "abm_adjoint", "abm_far_history", "abm_solve_noalloc",
-           "abm_plan_kernel_times"]
+           "abm_plan_kernel_times", "abm_solve_ext", "abm_solve_batched_ext"]
 KERNEL_KINDS = {"weights": 0, "far": 1, "near": 2, "single": 3, "adjoint": 4}
 
 
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
         lib.abm_weights.argtypes = [_vp, D, I, _vp, _vp, _vp, _vp]
         lib.abm_solve.argtypes = [_vp, D, D, I, _dp, _dp, _vp, _vp, _vp]
         lib.abm_solve_batched.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
+        lib.abm_solve_ext.argtypes = [_vp, _dp, D, I, _dp, _dp, _dp, _vp, _vp, _vp]
+        lib.abm_solve_batched_ext.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_solve_batched_host.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_adjoint.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp, _vp, _vp]
         lib.abm_far_history.argtypes = [_vp, D, _vp, LL, LL, LL, I, LL, LL, _vp, _vp, _vp]
@@ -235,7 +237,65 @@ class Plan:
             self.sync(stream)
         return (Y, YP) if want_yp or YP is not None else Y
 
+    def solve_ext(self, alpha, h, N, params, y0, y0d=None, Y=None, YP=None, want_yp=False, stream=None,
+                  sync=True):
+        """abm_solve_ext: the general problem of eq. (1) - alpha a scalar or one
+        order per component, each in (0, 2]; y0d the initial derivatives y'(0)
+        (None: zero), used by components of order above one."""
+        torch = _torch()
+        al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (self.d,)))
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        y = np.ascontiguousarray(y0, dtype=np.float64)
+        yd = None if y0d is None else np.ascontiguousarray(y0d, dtype=np.float64)
+        if p.size != self.np or y.size != self.d or (yd is not None and yd.size != self.d):
+            raise ValueError("params / y0 / y0d have the wrong size for this system")
+        if Y is None:
+            Y = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
+        if YP is None and want_yp:
+            YP = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
+        _check_out(Y, (N + 1, self.d), "Y", more_rows=True)
+        _check_out(YP, (N + 1, self.d), "YP", more_rows=True)
+        st = self.lib.abm_solve_ext(self.h, al.ctypes.data_as(_dp), float(h), int(N), p.ctypes.data_as(_dp),
+                                    y.ctypes.data_as(_dp), yd.ctypes.data_as(_dp) if yd is not None else None,
+                                    _dptr(Y), _dptr(YP), _stream_ptr(stream))
+        self._check(st, "abm_solve_ext")
+        if sync:
+            self.sync(stream)
+        return (Y, YP) if want_yp or YP is not None else Y
+
     # -- batched --
+    def solve_batched_ext(self, alpha, h, N, params, y0, y0d=None, Y=None, YP=None, want_yp=False, ldY=None,
+                          stream=None, sync=True):
+        """abm_solve_batched_ext: alpha (M,) or (M, d) orders in (0, 2] (host);
+        y0d (M, d) initial derivatives (copied to the device) or None."""
+        torch = _torch()
+        hh = np.ascontiguousarray(h, dtype=np.float64)
+        NN = np.ascontiguousarray(N, dtype=np.int32)
+        M = NN.size
+        al = np.asarray(alpha, dtype=np.float64)
+        al = np.ascontiguousarray(np.broadcast_to(al.reshape(M, -1), (M, self.d)))
+        if hh.size != M:
+            raise ValueError("alpha, h and N need one entry per trajectory")
+        params = _dev_f64(params, M * self.np, "params")
+        y0 = _dev_f64(y0, M * self.d, "y0")
+        yd = None if y0d is None else _dev_f64(y0d, M * self.d, "y0d")
+        if ldY is None:
+            ldY = int(NN.max()) + 1 if NN.size else 1
+        if Y is None:
+            Y = torch.zeros(M, ldY, self.d, dtype=torch.float64, device="cuda")
+        if YP is None and want_yp:
+            YP = torch.zeros(M, ldY, self.d, dtype=torch.float64, device="cuda")
+        _check_out(Y, (M, ldY, self.d), "Y")
+        _check_out(YP, (M, ldY, self.d), "YP")
+        self._ext_inputs = yd  # kept alive until the asynchronous solve has read it
+        st = self.lib.abm_solve_batched_ext(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
+                                            NN.ctypes.data_as(_ip), _dptr(params), _dptr(y0), _dptr(yd), _dptr(Y),
+                                            int(ldY), _dptr(YP), _stream_ptr(stream))
+        self._check(st, "abm_solve_batched_ext")
+        if sync:
+            self.sync(stream)
+        return (Y, YP) if want_yp or YP is not None else Y
+
     def solve_batched(self, alpha, h, N, params, y0, Y=None, YP=None, want_yp=False, ldY=None, stream=None,
                       sync=True):
         """alpha, h, N: host sequences (scheduling); params (M, np), y0 (M, d):

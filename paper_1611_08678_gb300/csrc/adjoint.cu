@@ -45,9 +45,9 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_setup_kernel(AdjArgs
   const TileDesc& T = A.tiles[tile];
   const int traj = T.traj[lane];
   const int src = traj >= 0 ? traj : T.traj[0];
-  const double alpha = A.bucket_alpha[T.bucket];
-  const double g = A.bucket_g[T.bucket];
-  const double* wc = A.bucket_c[T.bucket];
+  const double alpha = A.bucket_alpha[T.bucket * kMaxD];
+  const double g = A.bucket_g[T.bucket * kMaxD];
+  const double* wc = A.bucket_c[T.bucket * kMaxD];
   const long long N = A.N[src];
   const double h = A.h[src];
   const double hh = pow(h, alpha);
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_setup_kernel(AdjArgs
   const double mu = hh * g * jl;
   const bool act = traj >= 0;
   if (act) {
-    if (c == 0) A.hhat[traj] = hh;
+    if (c == 0) A.hhat[(size_t)traj * kMaxD] = hh;
 #pragma unroll
     for (int q = 0; q < NP; ++q) A.acc_dp[((size_t)traj * D + c) * NP + q] = hh * g * Q[c * NP + q] * lam;
     A.acc_dy0[(size_t)traj * D + c] = lam + mu;
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) adjoint_near_kern
   const TileDesc& T = A.tiles[tile];
   const int traj = T.traj[lane];
   const int src = traj >= 0 ? traj : T.traj[0];
-  const double* wb = A.bucket_b[T.bucket];
-  const double* wa = A.bucket_a[T.bucket];
+  const double* wb = A.bucket_b[T.bucket * kMaxD];
+  const double* wa = A.bucket_a[T.bucket * kMaxD];
   double* Xm = A.X + A.atiles[2 * tile].f_off;
   double* Xl = A.X + A.atiles[2 * tile + 1].f_off;
   for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
@@ -122,12 +122,12 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) adjoint_near_kern
   }
 
   if (chain) {
-    const double alpha = A.bucket_alpha[T.bucket];
-    const double* wc = A.bucket_c[T.bucket];
-    const double g = A.bucket_g[T.bucket];
+    const double alpha = A.bucket_alpha[T.bucket * kMaxD];
+    const double* wc = A.bucket_c[T.bucket * kMaxD];
+    const double g = A.bucket_g[T.bucket * kMaxD];
     const long long Ni = traj >= 0 ? (long long)A.N[traj] : -1;
     const double h = A.h[src];
-    const double hh = traj >= 0 ? A.hhat[traj] : 0.0;
+    const double hh = traj >= 0 ? A.hhat[(size_t)traj * kMaxD] : 0.0;
     double p[kMaxParams];
 #pragma unroll
     for (int k = 0; k < NP; ++k) p[k] = A.params[(size_t)src * NP + k];
@@ -317,8 +317,8 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_near_split_kernel(Ad
   const TileDesc& Td = A.tiles[tile];
   const int traj = Td.traj[tl];
   const int src = traj >= 0 ? traj : Td.traj[0];
-  const double* wb = A.bucket_b[Td.bucket];
-  const double* wa = A.bucket_a[Td.bucket];
+  const double* wb = A.bucket_b[Td.bucket * kMaxD];
+  const double* wa = A.bucket_a[Td.bucket * kMaxD];
   double* Xm = A.X + A.atiles[2 * tile].f_off;
   double* Xl = A.X + A.atiles[2 * tile + 1].f_off;
   for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
@@ -326,12 +326,12 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) adjoint_near_split_kernel(Ad
     Wm[0][m] = Xm[s * ld + part * ldc + m];
     Wl[0][m] = Xl[s * ld + part * ldc + m];
   }
-  const double alpha = A.bucket_alpha[Td.bucket];
-  const double* wc = A.bucket_c[Td.bucket];
-  const double g = A.bucket_g[Td.bucket];
+  const double alpha = A.bucket_alpha[Td.bucket * kMaxD];
+  const double* wc = A.bucket_c[Td.bucket * kMaxD];
+  const double g = A.bucket_g[Td.bucket * kMaxD];
   const long long Ni = traj >= 0 ? (long long)A.N[traj] : -1;
   const double h = A.h[src];
-  const double hh = traj >= 0 ? A.hhat[traj] : 0.0;
+  const double hh = traj >= 0 ? A.hhat[(size_t)traj * kMaxD] : 0.0;
   double p[kMaxParams];
 #pragma unroll
   for (int k = 0; k < NP; ++k) p[k] = A.params[(size_t)src * NP + k];

@@ -1,6 +1,7 @@
 // C ABI (include/abm.h): plans, argument checks, host-side scheduling and the
 // launch sequences of the single and batched paths.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -89,11 +90,13 @@ struct abm_plan_s {
   TileDesc* d_tiles = nullptr;
   double* d_h = nullptr;
   int* d_N = nullptr;
-  double* d_hhat = nullptr;
+  double* d_hhat = nullptr;         // [max_batch][kMaxD]
+  // per order group and component, entry [group * kMaxD + component]
   double* d_balpha = nullptr;
-  double* d_bg = nullptr;           // gathered g per bucket
-  const double** d_bptr = nullptr;  // [4][kMaxWeightSets] b,a,c pointers
-  const float** d_b32ptr = nullptr; // [2][kMaxWeightSets]
+  double* d_bg = nullptr;           // gathered g
+  int* d_btaylor = nullptr;         // per group: bit c = component c has order above one
+  const double** d_bptr = nullptr;  // [3][kMaxWeightSets * kMaxD] b, a, c pointers
+  const float** d_b32ptr = nullptr; // [2][kMaxWeightSets * kMaxD]
   // tensor-core far history (BF16 split precisions)
   __nv_bfloat16* Fsh = nullptr;     // [3][max_tiles*96][fsh_ld]
   long long fsh_ld = 0;
@@ -161,6 +164,8 @@ int sys_nparams(abm_system s) {
 }
 
 bool alpha_ok(double a) { return std::isfinite(a) && a > 0.0 && a <= 1.0; }
+// orders of the general problem (abm_solve_ext, abm_solve_batched_ext)
+bool order_ok(double a) { return std::isfinite(a) && a > 0.0 && a <= 2.0; }
 
 // Tracing: opens an event pair before a launch of `kind` (when profiling) and
 // closes it after; counts the launch.
@@ -304,52 +309,80 @@ abm_status far_history_tc(abm_plan p, double alpha, const double* F, long long r
 }
 
 // Host-side scheduling shared by the batched solve and its adjoint: argument
-// checks, alpha groups (one weight set each), column tiles of 32 trajectories
-// ordered by N, history offsets, and the device tables the kernels read.
+// checks, order groups (trajectories with the same order per component; one
+// weight set per distinct order), column tiles of 32 trajectories ordered by
+// N, history offsets, and the device tables the kernels read.
 struct Sched {
-  std::vector<double> ualpha;
-  std::vector<WeightSet*> ws;
+  std::vector<std::array<double, kMaxD>> groups;  // orders per group and component
+  std::vector<WeightSet*> ws;                     // [group * kMaxD + component]
   std::vector<TileDesc> tiles;
   int n_tiles = 0, nmax = 0, ksplit = 1;
+  bool per_comp = false;                          // some group's orders differ per component
   size_t hist_elems = 0;
 };
 
-abm_status schedule_batch(abm_plan p, int M, const double* alpha, const double* h, const int* N, long long ldY,
-                          cudaStream_t st, Sched& S, const char* who) {
+// alpha: M orders (astride = 1, every component) or M x d (astride = d), each
+// in (0, amax].
+abm_status schedule_batch(abm_plan p, int M, const double* alpha, int astride, double amax, const double* h,
+                          const int* N, long long ldY, cudaStream_t st, Sched& S, const char* who) {
   const int B = p->B, d = p->d;
+  auto order = [&](int i, int c) { return alpha[(size_t)i * astride + (astride > 1 ? c : 0)]; };
   int& nmax = S.nmax;
   nmax = 0;
   for (int i = 0; i < M; ++i) {
-    if (!alpha_ok(alpha[i]) || !(std::isfinite(h[i]) && h[i] > 0.0) || N[i] < 1 || N[i] > p->o.n_max)
-      return fail(p, ABM_ERR_INVALID_ARG, std::string(who) + ": trajectory " + std::to_string(i) +
-                                              " needs alpha in (0,1], finite h > 0, 1 <= N <= n_max");
+    bool ok = std::isfinite(h[i]) && h[i] > 0.0 && N[i] >= 1 && N[i] <= p->o.n_max;
+    for (int c = 0; c < d; ++c) ok = ok && std::isfinite(order(i, c)) && order(i, c) > 0.0 && order(i, c) <= amax;
+    if (!ok)
+      return fail(p, ABM_ERR_INVALID_ARG, std::string(who) + ": trajectory " + std::to_string(i) + " needs orders in (0," +
+                                              (amax > 1.0 ? "2" : "1") + "], finite h > 0, 1 <= N <= n_max");
     nmax = std::max(nmax, N[i]);
   }
   if (ldY < (long long)nmax + 1) return fail(p, ABM_ERR_INVALID_ARG, std::string(who) + ": ldY < max(N)+1");
-  // ---- alpha groups ----
-  std::vector<double>& ualpha = S.ualpha;
-  for (int i = 0; i < M; ++i)
-    if (std::find(ualpha.begin(), ualpha.end(), alpha[i]) == ualpha.end()) ualpha.push_back(alpha[i]);
-  if ((int)ualpha.size() > kMaxWeightSets)
-    return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": more distinct alpha values than weight sets");
-  std::vector<WeightSet*>& ws = S.ws;
-  ws.assign(ualpha.size(), nullptr);
-  for (size_t g = 0; g < ualpha.size(); ++g) {
-    abm_status rs = get_weights(p, ualpha[g], st, &ws[g]);
-    if (rs) return rs;
+  // ---- order groups ----
+  std::vector<int> group_of(M);
+  std::vector<double> values;  // distinct orders (one weight set each)
+  for (int i = 0; i < M; ++i) {
+    std::array<double, kMaxD> t{};
+    for (int c = 0; c < kMaxD; ++c) t[c] = order(i, c < d ? c : 0);
+    size_t g = std::find(S.groups.begin(), S.groups.end(), t) - S.groups.begin();
+    if (g == S.groups.size()) S.groups.push_back(t);
+    group_of[i] = (int)g;
+    for (int c = 0; c < d; ++c)
+      if (std::find(values.begin(), values.end(), t[c]) == values.end()) values.push_back(t[c]);
   }
+  const int n_groups = (int)S.groups.size();
+  if (n_groups > kMaxWeightSets || (int)values.size() > kMaxWeightSets)
+    return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": more than " + std::to_string(kMaxWeightSets) +
+                                            " distinct orders or order groups");
+  for (const auto& t : S.groups)
+    for (int c = 1; c < d; ++c)
+      if (t[c] != t[0]) S.per_comp = true;
+  if (S.per_comp && p->Fsh)
+    return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": the tensor-core far history (BF16X3/X6) takes one order "
+                                            "per trajectory; orders that differ per component need an FP64 or FP32 plan");
+  std::vector<WeightSet*>& ws = S.ws;
+  ws.assign((size_t)n_groups * kMaxD, nullptr);
+  for (int g = 0; g < n_groups; ++g)
+    for (int c = 0; c < d; ++c) {
+      // distinct orders <= the number of weight slots, so the least recently
+      // used slot get_weights reuses never holds an order of this batch
+      abm_status rs = get_weights(p, S.groups[g][c], st, &ws[(size_t)g * kMaxD + c]);
+      if (rs) return rs;
+    }
+  for (int g = 0; g < n_groups; ++g)
+    for (int c = d; c < kMaxD; ++c) ws[(size_t)g * kMaxD + c] = ws[(size_t)g * kMaxD];
   // ---- column tiles: per group, ordered by N descending, 32 trajectories each ----
   std::vector<TileDesc>& tiles = S.tiles;
   tiles.clear();
-  for (size_t g = 0; g < ualpha.size(); ++g) {
+  for (int g = 0; g < n_groups; ++g) {
     std::vector<int> idx;
     for (int i = 0; i < M; ++i)
-      if (alpha[i] == ualpha[g]) idx.push_back(i);
+      if (group_of[i] == g) idx.push_back(i);
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return N[x] > N[y]; });
     for (size_t q = 0; q < idx.size(); q += kTrajPerTile) {
       TileDesc t{};
       for (int l = 0; l < kTrajPerTile; ++l) t.traj[l] = (q + l < idx.size()) ? idx[q + l] : -1;
-      t.bucket = (int)g;
+      t.bucket = g;
       t.n_tile = N[idx[q]];
       tiles.push_back(t);
     }
@@ -368,33 +401,41 @@ abm_status schedule_batch(abm_plan p, int M, const double* alpha, const double* 
   const int n_tiles = (int)tiles.size();
   S.n_tiles = n_tiles;
   S.hist_elems = off;
-  if (p->Fsh && n_tiles > p->max_tiles) return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": too many tiles");
   int& ksplit = S.ksplit;
   ksplit = std::max(1, std::min(16, (2 * p->sms + n_tiles - 1) / n_tiles));
   while ((size_t)ksplit * n_tiles * 2 * B * kTrajPerTile * d > p->farb_cap && ksplit > 1) --ksplit;
-  // ---- device tables ----
-  std::vector<double> balpha(ualpha), bg(ualpha.size());
-  std::vector<const double*> bptr(3 * kMaxWeightSets, nullptr);
-  std::vector<const float*> b32ptr(2 * kMaxWeightSets, nullptr);
-  for (size_t g = 0; g < ualpha.size(); ++g) {
-    bptr[g] = ws[g]->b;
-    bptr[kMaxWeightSets + g] = ws[g]->a;
-    bptr[2 * kMaxWeightSets + g] = ws[g]->c;
-    b32ptr[g] = ws[g]->b32;
-    b32ptr[kMaxWeightSets + g] = ws[g]->a32;
-    CK(cudaMemcpyAsync(p->d_bg + g, ws[g]->g, sizeof(double), cudaMemcpyDeviceToDevice, st), "g copy");
-  }
+  // ---- device tables: entry [group * kMaxD + component] ----
+  const size_t NT = (size_t)kMaxWeightSets * kMaxD;
+  std::vector<double> balpha(NT, 0.0);
+  std::vector<int> btaylor(kMaxWeightSets, 0);
+  std::vector<const double*> bptr(3 * NT, nullptr);
+  std::vector<const float*> b32ptr(2 * NT, nullptr);
+  for (int g = 0; g < n_groups; ++g)
+    for (int c = 0; c < kMaxD; ++c) {
+      const size_t e = (size_t)g * kMaxD + c;
+      const WeightSet* w = ws[e];
+      balpha[e] = S.groups[g][c];
+      if (c < d && S.groups[g][c] > 1.0) btaylor[g] |= 1 << c;
+      bptr[e] = w->b;
+      bptr[NT + e] = w->a;
+      bptr[2 * NT + e] = w->c;
+      b32ptr[e] = w->b32;
+      b32ptr[NT + e] = w->a32;
+      CK(cudaMemcpyAsync(p->d_bg + e, w->g, sizeof(double), cudaMemcpyDeviceToDevice, st), "g copy");
+    }
   CK(cudaMemcpyAsync(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, st), "tiles");
   CK(cudaMemcpyAsync(p->d_h, h, M * sizeof(double), cudaMemcpyHostToDevice, st), "h");
   CK(cudaMemcpyAsync(p->d_N, N, M * sizeof(int), cudaMemcpyHostToDevice, st), "N");
-  CK(cudaMemcpyAsync(p->d_balpha, balpha.data(), balpha.size() * sizeof(double), cudaMemcpyHostToDevice, st), "alpha");
+  CK(cudaMemcpyAsync(p->d_balpha, balpha.data(), n_groups * kMaxD * sizeof(double), cudaMemcpyHostToDevice, st),
+     "alpha");
+  CK(cudaMemcpyAsync(p->d_btaylor, btaylor.data(), n_groups * sizeof(int), cudaMemcpyHostToDevice, st), "taylor");
   CK(cudaMemcpyAsync(p->d_bptr, bptr.data(), bptr.size() * sizeof(double*), cudaMemcpyHostToDevice, st), "ptrs");
   CK(cudaMemcpyAsync(p->d_b32ptr, b32ptr.data(), b32ptr.size() * sizeof(float*), cudaMemcpyHostToDevice, st), "ptrs");
   if (p->Fsh) {
-    std::vector<CUtensorMap> mw(ualpha.size() * 3);
-    for (size_t g = 0; g < ualpha.size(); ++g)
+    std::vector<CUtensorMap> mw((size_t)n_groups * 3);
+    for (int g = 0; g < n_groups; ++g)
       for (int q = 0; q < 3; ++q)
-        if (!make_tmap_bf16(&mw[g * 3 + q], ws[g]->Wx + (size_t)q * 128 * p->Lx, 64,
+        if (!make_tmap_bf16(&mw[g * 3 + q], ws[(size_t)g * kMaxD]->Wx + (size_t)q * 128 * p->Lx, 64,
                             (unsigned long long)(2 * p->Lx), 128))
           return fail(p, ABM_ERR_CUDA, std::string(who) + ": tensor map of the Toeplitz pieces");
     CK(cudaMemcpyAsync(p->d_tmapW, mw.data(), mw.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st), "tmaps");
@@ -484,26 +525,30 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
 }
 
 // Kernel arguments of one batched solve (tables from schedule_batch).
-BatchArgs batch_args(abm_plan p, const Sched& S, const double* params, const double* y0, double* Y, double* YP,
-                     long long ldY) {
+BatchArgs batch_args(abm_plan p, const Sched& S, const double* params, const double* y0, const double* y0d,
+                     double* Y, double* YP, long long ldY) {
   const int d = p->d;
+  const size_t NT = (size_t)kMaxWeightSets * kMaxD;
   BatchArgs A{};
   A.tiles = p->d_tiles;
   A.n_tiles = S.n_tiles;
   A.B = p->B;
   A.ksplit = S.ksplit;
   A.far_k0 = 1;
+  A.per_comp = S.per_comp ? 1 : 0;
   A.bucket_alpha = p->d_balpha;
   A.bucket_b = p->d_bptr;
-  A.bucket_a = p->d_bptr + kMaxWeightSets;
-  A.bucket_c = p->d_bptr + 2 * kMaxWeightSets;
+  A.bucket_a = p->d_bptr + NT;
+  A.bucket_c = p->d_bptr + 2 * NT;
   A.bucket_b32 = p->d_b32ptr;
-  A.bucket_a32 = p->d_b32ptr + kMaxWeightSets;
+  A.bucket_a32 = p->d_b32ptr + NT;
   A.bucket_g = p->d_bg;
+  A.bucket_taylor = p->d_btaylor;
   A.h = p->d_h;
   A.N = p->d_N;
   A.params = params;
   A.y0 = y0;
+  A.y0d = y0d;
   A.hhat = p->d_hhat;
   A.F = p->Fb;
   A.F32 = (p->o.prec == ABM_PREC_FP32_FAR) ? p->Fb32 : nullptr;
@@ -609,11 +654,12 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
         !alloc((void**)&p->d_tiles, (size_t)p->max_tiles * sizeof(TileDesc)) ||
         !alloc((void**)&p->d_h, (size_t)o->max_batch * sizeof(double)) ||
         !alloc((void**)&p->d_N, (size_t)o->max_batch * sizeof(int)) ||
-        !alloc((void**)&p->d_hhat, (size_t)o->max_batch * sizeof(double)) ||
-        !alloc((void**)&p->d_balpha, kMaxWeightSets * sizeof(double)) ||
-        !alloc((void**)&p->d_bg, kMaxWeightSets * sizeof(double)) ||
-        !alloc((void**)&p->d_bptr, 3 * kMaxWeightSets * sizeof(double*)) ||
-        !alloc((void**)&p->d_b32ptr, 2 * kMaxWeightSets * sizeof(float*)))
+        !alloc((void**)&p->d_hhat, (size_t)o->max_batch * kMaxD * sizeof(double)) ||
+        !alloc((void**)&p->d_balpha, kMaxWeightSets * kMaxD * sizeof(double)) ||
+        !alloc((void**)&p->d_bg, kMaxWeightSets * kMaxD * sizeof(double)) ||
+        !alloc((void**)&p->d_btaylor, kMaxWeightSets * sizeof(int)) ||
+        !alloc((void**)&p->d_bptr, 3 * kMaxWeightSets * kMaxD * sizeof(double*)) ||
+        !alloc((void**)&p->d_b32ptr, 2 * kMaxWeightSets * kMaxD * sizeof(float*)))
       return cleanup_fail(ABM_ERR_OOM);
     if (tc_prec) {
       p->Lbase = (long long)((o->n_max + 63) / 64) * 64;
@@ -656,7 +702,7 @@ abm_status abm_plan_destroy(abm_plan p) {
   cudaFree(p->F1); cudaFree(p->far1); cudaFree(p->part1); cudaFree(p->tickets); cudaFree(p->hhat1);
   cudaFree(p->Fb); cudaFree(p->Fb32); cudaFree(p->farb); cudaFree(p->d_tiles); cudaFree(p->d_h);
   cudaFree(p->d_N); cudaFree(p->d_hhat); cudaFree(p->d_balpha); cudaFree(p->d_bg);
-  cudaFree(p->d_bptr); cudaFree(p->d_b32ptr); cudaFree(p->status);
+  cudaFree(p->d_bptr); cudaFree(p->d_b32ptr); cudaFree(p->d_btaylor); cudaFree(p->status);
   if (p->side) cudaStreamDestroy(p->side);
   for (int i = 0; i < kEventRing; ++i) {
     if (p->ev_near[i]) cudaEventDestroy(p->ev_near[i]);
@@ -685,8 +731,8 @@ abm_status abm_plan_sync(abm_plan p, void* stream, int64_t* where) {
 
 abm_status abm_weights(abm_plan p, double alpha, int M, double* b, double* a, double* c, void* stream) {
   if (!p) return ABM_ERR_INVALID_ARG;
-  if (!alpha_ok(alpha) || M < 0 || !b || !a || !c)
-    return fail(p, ABM_ERR_INVALID_ARG, "abm_weights: alpha must be in (0,1], M >= 0, arrays non-null");
+  if (!order_ok(alpha) || M < 0 || !b || !a || !c)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_weights: alpha must be in (0,2], M >= 0, arrays non-null");
   CK(launch_weights(alpha, M, b, a, c, nullptr, (cudaStream_t)stream), "weights kernel");
   return ABM_OK;
 }
@@ -723,81 +769,131 @@ abm_status abm_far_history(abm_plan p, double alpha, const double* F, long long 
   return ABM_OK;
 }
 
-abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* params, const double* y0,
-                     double* Y, double* YP, void* stream) {
-  if (!p) return ABM_ERR_INVALID_ARG;
-  if (!alpha_ok(alpha) || !(std::isfinite(h) && h > 0.0) || N < 1 || N > p->o.n_max || !params || !y0 || !Y)
-    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve: need alpha in (0,1], finite h > 0, 1 <= N <= n_max, "
-                                        "non-null params/y0/Y");
+}  // extern "C"
+
+namespace {
+
+// The single-trajectory solve behind abm_solve and abm_solve_ext: alpha holds
+// one order per component (in (0, 2]); y0d the initial derivatives (NULL:
+// zero), used by components of order above one.
+abm_status solve_single(abm_plan p, const char* who, const double* alpha, double h, int N, const double* params,
+                        const double* y0, const double* y0d, double* Y, double* YP, cudaStream_t st) {
   TrajParams tp{};
   for (int i = 0; i < p->np; ++i) {
-    if (!std::isfinite(params[i])) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve: non-finite parameter");
+    if (!std::isfinite(params[i])) return fail(p, ABM_ERR_INVALID_ARG, std::string(who) + ": non-finite parameter");
     tp.p[i] = params[i];
   }
+  int taylor_mask = 0;
   for (int i = 0; i < p->d; ++i) {
-    if (!std::isfinite(y0[i])) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve: non-finite y0");
+    if (!std::isfinite(y0[i]) || (y0d && !std::isfinite(y0d[i])))
+      return fail(p, ABM_ERR_INVALID_ARG, std::string(who) + ": non-finite y0 or y0d");
     tp.y0[i] = y0[i];
+    if (alpha[i] > 1.0) {
+      taylor_mask |= 1 << i;
+      tp.y0d[i] = y0d ? y0d[i] : 0.0;
+    }
   }
-  cudaStream_t st = (cudaStream_t)stream;
-  WeightSet* w;
-  abm_status rs = get_weights(p, alpha, st, &w);
-  if (rs) return rs;
+  // one weight set per distinct order
+  PersistArgs A{};
+  int nc = 1;
+  for (int i = 0; i < p->d; ++i) {
+    if (alpha[i] != alpha[0]) nc = p->d;
+    int same = -1;
+    for (int j = 0; j < i && same < 0; ++j)
+      if (alpha[j] == alpha[i]) same = j;
+    if (same >= 0) {
+      A.b[i] = A.b[same];
+      A.a[i] = A.a[same];
+      A.c[i] = A.c[same];
+      A.g[i] = A.g[same];
+      continue;
+    }
+    WeightSet* w = nullptr;  // the least recently used set is reused: never one taken above
+    abm_status rs = get_weights(p, alpha[i], st, &w);
+    if (rs) return rs;
+    A.b[i] = w->b;
+    A.a[i] = w->a;
+    A.c[i] = w->c;
+    A.g[i] = w->g;
+  }
   // one cooperative launch: CTA 0 steps, CTAs 1..Gp-1 compute the far history
   CK(cudaMemsetAsync(p->pflags, 0, (1 + kPersistRing) * sizeof(unsigned long long), st), "flags reset");
-  PersistArgs A{};
   A.F = p->F1;
   A.Y = Y;
   A.YP = YP;
-  A.b = w->b;
-  A.a = w->a;
-  A.c = w->c;
-  A.g = w->g;
   A.partial = p->ppartial;
   A.flags = p->pflags;
   A.status = p->status;
   A.tp = tp;
-  A.alpha = alpha;
+  for (int i = 0; i < kMaxD; ++i) A.alpha[i] = alpha[i < p->d ? i : 0];
   A.h = h;
+  A.taylor_mask = taylor_mask;
   A.N = N;
   A.spin_budget = p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL;
   A.withhold_tile = p->o.test_withhold_tile > 0 ? p->o.test_withhold_tile - 1 : -1;
   A.passes = p->o.corrector_passes > 1 ? p->o.corrector_passes : 1;
   {
     Trace tr(p, ABM_KERNEL_SINGLE, st);
-    CK(launch_persistent(p->sys, A, p->Gp, st), "persistent single-trajectory kernel");
+    CK(launch_persistent(p->sys, nc, A, p->Gp, st), "persistent single-trajectory kernel");
   }
   return ABM_OK;
 }
 
-abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const double* h, const int* N,
-                             const double* params, const double* y0, double* Y, long long ldY, double* YP,
-                             void* stream) {
+}  // namespace
+
+extern "C" {
+
+abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* params, const double* y0,
+                     double* Y, double* YP, void* stream) {
   if (!p) return ABM_ERR_INVALID_ARG;
-  if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y)
-    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: need 1 <= M <= max_batch and non-null arrays");
-  cudaStream_t st = (cudaStream_t)stream;
+  if (!alpha_ok(alpha) || !(std::isfinite(h) && h > 0.0) || N < 1 || N > p->o.n_max || !params || !y0 || !Y)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve: need alpha in (0,1], finite h > 0, 1 <= N <= n_max, "
+                                        "non-null params/y0/Y");
+  const double al[kMaxD] = {alpha, alpha, alpha};
+  return solve_single(p, "abm_solve", al, h, N, params, y0, nullptr, Y, YP, (cudaStream_t)stream);
+}
+
+abm_status abm_solve_ext(abm_plan p, const double* alpha, double h, int N, const double* params, const double* y0,
+                         const double* y0d, double* Y, double* YP, void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (!alpha || !(std::isfinite(h) && h > 0.0) || N < 1 || N > p->o.n_max || !params || !y0 || !Y)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_ext: need finite h > 0, 1 <= N <= n_max, "
+                                        "non-null alpha/params/y0/Y");
+  for (int i = 0; i < p->d; ++i)
+    if (!order_ok(alpha[i])) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_ext: every order must be in (0, 2]");
+  return solve_single(p, "abm_solve_ext", alpha, h, N, params, y0, y0d, Y, YP, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// abm_solve_batched / abm_solve_batched_ext: alpha holds M orders (astride 1)
+// or M x d (astride d), y0d the initial derivatives (device, may be null).
+abm_status solve_batched_impl(abm_plan p, const char* who, int M, const double* alpha, int astride, double amax,
+                              const double* h, const int* N, const double* params, const double* y0,
+                              const double* y0d, double* Y, long long ldY, double* YP, cudaStream_t st) {
   // with use_graph, a call whose arguments equal those of the captured call
   // replays the graph (the device tables it reads are still in place)
   std::vector<unsigned char> key;
   if (p->o.use_graph) {
     key_append(key, &M, 1);
-    key_append(key, alpha, M);
+    key_append(key, &astride, 1);
+    key_append(key, alpha, (size_t)M * astride);
     key_append(key, h, M);
     key_append(key, N, M);
-    const void* ptrs[5] = {params, y0, Y, YP, nullptr};
+    const void* ptrs[5] = {params, y0, Y, YP, y0d};
     key_append(key, ptrs, 5);
     key_append(key, &ldY, 1);
     if (p->graph_exec && key == p->graph_key) {
-      for (int i = 0; i < M; ++i)  // the same host checks as an uncaptured call
-        if (!alpha_ok(alpha[i]) || N[i] < 1 || N[i] > p->o.n_max) return fail(p, ABM_ERR_INVALID_ARG, "bad args");
-      CK(cudaGraphLaunch(p->graph_exec, st), "graph launch");
+      CK(cudaGraphLaunch(p->graph_exec, st), "graph launch");  // the key fixes every value checked before
       return ABM_OK;
     }
   }
   Sched S;
-  abm_status rs = schedule_batch(p, M, alpha, h, N, ldY, st, S, "abm_solve_batched");
+  abm_status rs = schedule_batch(p, M, alpha, astride, amax, h, N, ldY, st, S, who);
   if (rs) return rs;
-  const BatchArgs A = batch_args(p, S, params, y0, Y, YP, ldY);
+  const BatchArgs A = batch_args(p, S, params, y0, y0d, Y, YP, ldY);
   if (!p->o.use_graph) return enqueue_batched(p, S, A, st);
   // capture the launch sequence on the plan's side stream, after the uploads
   if (p->graph_exec) {
@@ -822,6 +918,30 @@ abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const doubl
   return ABM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+abm_status abm_solve_batched(abm_plan p, int M, const double* alpha, const double* h, const int* N,
+                             const double* params, const double* y0, double* Y, long long ldY, double* YP,
+                             void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched: need 1 <= M <= max_batch and non-null arrays");
+  return solve_batched_impl(p, "abm_solve_batched", M, alpha, 1, 1.0, h, N, params, y0, nullptr, Y, ldY, YP,
+                            (cudaStream_t)stream);
+}
+
+abm_status abm_solve_batched_ext(abm_plan p, int M, const double* alpha, const double* h, const int* N,
+                                 const double* params, const double* y0, const double* y0d, double* Y,
+                                 long long ldY, double* YP, void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched_ext: need 1 <= M <= max_batch and non-null arrays");
+  return solve_batched_impl(p, "abm_solve_batched_ext", M, alpha, p->d, 2.0, h, N, params, y0, y0d, Y, ldY, YP,
+                            (cudaStream_t)stream);
+}
+
 abm_status abm_solve_batched_host(abm_plan p, int M, const double* alpha, const double* h, const int* N,
                                   const double* params, const double* y0, double* Y, long long ldY, double* YP,
                                   void* stream) {
@@ -841,7 +961,7 @@ abm_status abm_solve_batched_host(abm_plan p, int M, const double* alpha, const 
   }
   if (YP && !p->hio_YP) CK(cudaMalloc(&p->hio_YP, (size_t)p->o.max_batch * ldd * d * sizeof(double)), "host-io YP");
   Sched S;
-  abm_status rs = schedule_batch(p, M, alpha, h, N, ldY, st, S, "abm_solve_batched_host");
+  abm_status rs = schedule_batch(p, M, alpha, 1, 1.0, h, N, ldY, st, S, "abm_solve_batched_host");
   if (rs) return rs;
   // inputs up, then the solve with each finished trajectory copied out behind
   // the time tile that completes it
@@ -863,7 +983,7 @@ abm_status abm_solve_batched_host(abm_plan p, int M, const double* alpha, const 
   out.Yd = p->hio_Y;
   out.YPd = YP ? p->hio_YP : nullptr;
   out.ldd = ldd;
-  const BatchArgs A = batch_args(p, S, p->hio_params, p->hio_y0, p->hio_Y, YP ? p->hio_YP : nullptr, ldd);
+  const BatchArgs A = batch_args(p, S, p->hio_params, p->hio_y0, nullptr, p->hio_Y, YP ? p->hio_YP : nullptr, ldd);
   rs = enqueue_batched(p, S, A, st, &out);
   if (rs) return rs;
   CK(cudaEventRecord(p->hio_done, p->copy_st), "event");
@@ -919,7 +1039,7 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
   cudaStream_t st = (cudaStream_t)stream;
   const int B = p->B, d = p->d;
   Sched S;
-  abm_status rs = schedule_batch(p, M, alpha, h, N, ldY, st, S, "abm_adjoint");
+  abm_status rs = schedule_batch(p, M, alpha, 1, 1.0, h, N, ldY, st, S, "abm_adjoint");
   if (rs) return rs;
   const int n_tiles = S.n_tiles;
   const bool tc_prec = p->Fsh != nullptr;
@@ -961,8 +1081,8 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
   A.B = p->B;
   A.bucket_alpha = p->d_balpha;
   A.bucket_b = p->d_bptr;
-  A.bucket_a = p->d_bptr + kMaxWeightSets;
-  A.bucket_c = p->d_bptr + 2 * kMaxWeightSets;
+  A.bucket_a = p->d_bptr + (size_t)kMaxWeightSets * kMaxD;
+  A.bucket_c = p->d_bptr + 2 * (size_t)kMaxWeightSets * kMaxD;
   A.bucket_g = p->d_bg;
   A.h = p->d_h;
   A.N = p->d_N;
@@ -995,9 +1115,10 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
   F.far_k0 = 0;  // reversed row 0 (the k = N terms) is an ordinary row here
   F.bucket_alpha = p->d_balpha;
   F.bucket_b = p->d_bptr;
-  F.bucket_a = p->d_bptr + kMaxWeightSets;
-  F.bucket_c = p->d_bptr + 2 * kMaxWeightSets;
+  F.bucket_a = p->d_bptr + (size_t)kMaxWeightSets * kMaxD;
+  F.bucket_c = p->d_bptr + 2 * (size_t)kMaxWeightSets * kMaxD;
   F.bucket_g = p->d_bg;
+  F.bucket_taylor = p->d_btaylor;
   F.F = p->Xadj;
   F.far = p->farb;
   F.status = p->status;

@@ -12,6 +12,8 @@
 //   k = 0 terms b_n f_0, c_n f_0 : near kernel, FP64
 // (Sec. 2 formulas; the split is the per-tile form of the partial sums the
 // paper gathers across processes, Sec. 3 Fig. 2.)
+#include <type_traits>
+
 #include "bf16split.cuh"
 #include "common.cuh"
 #include "systems.cuh"
@@ -30,7 +32,8 @@ __global__ void batched_setup_kernel(BatchArgs A) {
   const TileDesc& T = A.tiles[tile];
   int traj = T.traj[lane];
   int src = traj >= 0 ? traj : T.traj[0];
-  double alpha = A.bucket_alpha[T.bucket];
+  const int bk = T.bucket * kMaxD;
+  double alpha = A.bucket_alpha[bk];
   double p[kMaxParams], y0[D], f0[D];
 #pragma unroll
   for (int q = 0; q < S::NP; ++q) p[q] = A.params[(size_t)src * S::NP + q];
@@ -46,7 +49,8 @@ __global__ void batched_setup_kernel(BatchArgs A) {
     for (int c = 0; c < D; ++c) F32[lane * D + c] = (float)f0[c];
   }
   if (traj >= 0) {
-    A.hhat[traj] = pow(A.h[traj], alpha);
+#pragma unroll
+    for (int c = 0; c < D; ++c) A.hhat[(size_t)traj * kMaxD + c] = pow(A.h[traj], A.bucket_alpha[bk + c]);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       A.Y[(size_t)traj * A.ldY * D + c] = y0[c];
@@ -86,8 +90,8 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
   double (*Rp)[HSX][ld] = reinterpret_cast<double (*)[HSX][ld]>(near_dyn + 65 * ld);
   double (*Rc)[HSX][ld] = reinterpret_cast<double (*)[HSX][ld]>(near_dyn + (65 + 2 * HS) * ld);
   __shared__ double ysh[2][D][32], ysh2[2][D][32];  // predictor / corrector exchange
-  __shared__ double wsb[65], wsa[65];               // lags 0..64 of this tile's weights
-  __shared__ double bns[64], cns[64];               // b_n, c_n of this tile's targets
+  // per component: lags 0..64 of its weights, b_n and c_n of this tile's targets
+  __shared__ double wsb_[D][65], wsa_[D][65], bns_[D][64], cns_[D][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool chain = warp < D;
   const int c = chain ? warp : (warp - D) % D;  // component (column group)
@@ -96,14 +100,22 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
   const TileDesc& T = A.tiles[tile];
   const int traj = T.traj[lane];
   const int src = traj >= 0 ? traj : T.traj[0];
-  const double alpha = A.bucket_alpha[T.bucket];
-  const double* __restrict__ wb = A.bucket_b[T.bucket];
-  const double* __restrict__ wa = A.bucket_a[T.bucket];
-  const double* __restrict__ wc = A.bucket_c[T.bucket];
+  const int bk = T.bucket * kMaxD;
+  const double alpha = A.bucket_alpha[bk];  // the system's own use of alpha
   const int col = lane * D + c;  // this thread's history column
   double* __restrict__ F = A.F + T.f_off;
-  for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
-  for (int m = threadIdx.x; m < 64; m += NT) { bns[m] = wb[s + m]; cns[m] = wc[s + m]; }
+  for (int m = threadIdx.x; m < D * 65; m += NT) {
+    wsb_[m / 65][m % 65] = A.bucket_b[bk + m / 65][m % 65];
+    wsa_[m / 65][m % 65] = A.bucket_a[bk + m / 65][m % 65];
+  }
+  for (int m = threadIdx.x; m < D * 64; m += NT) {
+    bns_[m / 64][m % 64] = A.bucket_b[bk + m / 64][s + m % 64];
+    cns_[m / 64][m % 64] = A.bucket_c[bk + m / 64][s + m % 64];
+  }
+  const double* wsb = wsb_[c];  // this warp's component
+  const double* wsa = wsa_[c];
+  const double* bns = bns_[c];
+  const double* cns = cns_[c];
   for (int m = threadIdx.x; m < ld; m += NT) Fw[0][m] = F[s * ld + m];
   for (int m = threadIdx.x; m < HS * ld; m += NT) {  // step 0 has no earlier window rows (helpers)
     Rp[0][m / ld][m % ld] = 0.0;
@@ -112,14 +124,17 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
   const int kfirst = s > 1 ? 0 : 1;  // window rows relative to s (row 0 is f_0 when s = 0)
 
   if (chain) {
-    const double g = A.bucket_g[T.bucket];
+    const double g = A.bucket_g[bk + c];
     const long long Ntraj = traj >= 0 ? (long long)A.N[traj] : 0;
     const double h = A.h[src];
-    const double hh = traj >= 0 ? A.hhat[traj] : pow(h, alpha);
+    const double hh = traj >= 0 ? A.hhat[(size_t)traj * kMaxD + c] : pow(h, A.bucket_alpha[bk + c]);
     double p[kMaxParams];
 #pragma unroll
     for (int k = 0; k < S::NP; ++k) p[k] = A.params[(size_t)src * S::NP + k];
-    const double y0c = A.y0[(size_t)src * D + c];
+    const double y0c0 = A.y0[(size_t)src * D + c];
+    // Taylor sum of the initial values (eq. 2): y0, plus t y'(0) for an order above one
+    const bool taylor2 = (A.bucket_taylor[T.bucket] >> c) & 1;
+    const double y0dc = taylor2 && A.y0d ? A.y0d[(size_t)src * D + c] : 0.0;
     float* __restrict__ F32 = A.F32 ? A.F32 + T.f_off : nullptr;
     const double F0c = F[col];
     const double* __restrict__ farP = A.far + (((size_t)tile * 2) * A.B) * ld + col;
@@ -169,6 +184,7 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
         sc += sc1;
       }
       const double t1 = (double)(n + 1) * h;
+      const double y0c = taylor2 ? fma(t1, y0dc, y0c0) : y0c0;
       const double yp = fma(hh, sp, y0c);
       ysh[par][c][lane] = yp;
       asm volatile("bar.sync 1, %0;" ::"n"(32 * D) : "memory");
@@ -283,8 +299,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
   constexpr int ldc = T * D;                // columns of this CTA
   __shared__ double Fw[65][ldc];            // f rows s..s+64 of this CTA's columns
   __shared__ double ysh[2][D][T], ysh2[2][D][T];
-  __shared__ double wsb[65], wsa[65];
-  __shared__ double bns[64], cns[64];
+  __shared__ double wsb_[D][65], wsa_[D][65], bns_[D][64], cns_[D][64];  // per component
   const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;  // component, lane
   const int j = lane / L, l = lane % L;                      // trajectory of the part, lag slice
   const int tile = blockIdx.x / L, part = blockIdx.x % L;
@@ -292,26 +307,37 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
   const int tl = part * T + j;               // trajectory lane in the tile
   const int traj = Td.traj[tl];
   const int src = traj >= 0 ? traj : Td.traj[0];
-  const double alpha = A.bucket_alpha[Td.bucket];
-  const double* __restrict__ wb = A.bucket_b[Td.bucket];
-  const double* __restrict__ wa = A.bucket_a[Td.bucket];
-  const double* __restrict__ wc = A.bucket_c[Td.bucket];
+  const int bk = Td.bucket * kMaxD;
+  const double alpha = A.bucket_alpha[bk];  // the system's own use of alpha
   const int col = tl * D + c;                // column in the tile history
   const int cloc = j * D + c;                // column in this CTA's window
   double* __restrict__ F = A.F + Td.f_off;
   constexpr int NT = 32 * D;
-  for (int m = threadIdx.x; m < 65; m += NT) { wsb[m] = wb[m]; wsa[m] = wa[m]; }
-  for (int m = threadIdx.x; m < 64; m += NT) { bns[m] = wb[s + m]; cns[m] = wc[s + m]; }
+  for (int m = threadIdx.x; m < D * 65; m += NT) {
+    wsb_[m / 65][m % 65] = A.bucket_b[bk + m / 65][m % 65];
+    wsa_[m / 65][m % 65] = A.bucket_a[bk + m / 65][m % 65];
+  }
+  for (int m = threadIdx.x; m < D * 64; m += NT) {
+    bns_[m / 64][m % 64] = A.bucket_b[bk + m / 64][s + m % 64];
+    cns_[m / 64][m % 64] = A.bucket_c[bk + m / 64][s + m % 64];
+  }
+  const double* wsb = wsb_[c];  // this warp's component
+  const double* wsa = wsa_[c];
+  const double* bns = bns_[c];
+  const double* cns = cns_[c];
   for (int m = threadIdx.x; m < ldc; m += NT) Fw[0][m] = F[s * ldt + part * ldc + m];
   const int kfirst = s > 1 ? 0 : 1;  // window rows relative to s (row 0 is f_0 when s = 0)
-  const double g = A.bucket_g[Td.bucket];
+  const double g = A.bucket_g[bk + c];
   const long long Ntraj = traj >= 0 ? (long long)A.N[traj] : 0;
   const double h = A.h[src];
-  const double hh = traj >= 0 ? A.hhat[traj] : pow(h, alpha);
+  const double hh = traj >= 0 ? A.hhat[(size_t)traj * kMaxD + c] : pow(h, A.bucket_alpha[bk + c]);
   double p[kMaxParams];
 #pragma unroll
   for (int k = 0; k < S::NP; ++k) p[k] = A.params[(size_t)src * S::NP + k];
-  const double y0c = A.y0[(size_t)src * D + c];
+  const double y0c0 = A.y0[(size_t)src * D + c];
+  // Taylor sum of the initial values (eq. 2): y0, plus t y'(0) for an order above one
+  const bool taylor2 = (A.bucket_taylor[Td.bucket] >> c) & 1;
+  const double y0dc = taylor2 && A.y0d ? A.y0d[(size_t)src * D + c] : 0.0;
   float* __restrict__ F32 = A.F32 ? A.F32 + Td.f_off : nullptr;
   const double F0c = F[col];
   const double* __restrict__ farP = A.far + (((size_t)tile * 2) * A.B) * ldt + col;
@@ -360,6 +386,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
       nxc = sum_parts(farP + far_c_off + (size_t)(i + 1) * ldt, A.ksplit, far_q_stride);
     }
     const double t1 = (double)(n + 1) * h;
+    const double y0c = taylor2 ? fma(t1, y0dc, y0c0) : y0c0;
     const double yp = fma(hh, sp, y0c);
     if (l == 0) ysh[par][c][j] = yp;
     asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
@@ -437,8 +464,8 @@ __global__ void __launch_bounds__(256) batched_far_fp64_kernel(BatchArgs A, long
   constexpr int ld = kTrajPerTile * D;
   const int tile = blockIdx.x, q = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TileDesc& T = A.tiles[tile];
-  const double* __restrict__ wb = A.bucket_b[T.bucket];
-  const double* __restrict__ wa = A.bucket_a[T.bucket];
+  const double* __restrict__ wb = A.bucket_b[T.bucket * kMaxD];
+  const double* __restrict__ wa = A.bucket_a[T.bucket * kMaxD];
   const double* __restrict__ F = A.F + T.f_off;
   // history rows [1, s) split into ksplit chunks
   const long long K = s - A.far_k0;
@@ -490,8 +517,8 @@ __global__ void __launch_bounds__(512) batched_far_fp32_kernel(BatchArgs A, long
   constexpr int ld = kTrajPerTile * D;
   const int tile = blockIdx.x, q = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TileDesc& T = A.tiles[tile];
-  const float* __restrict__ wb = A.bucket_b32[T.bucket];
-  const float* __restrict__ wa = A.bucket_a32[T.bucket];
+  const float* __restrict__ wb = A.bucket_b32[T.bucket * kMaxD];
+  const float* __restrict__ wa = A.bucket_a32[T.bucket * kMaxD];
   const float* __restrict__ F = A.F32 + T.f_off;
   const long long K = s - A.far_k0;
   const long long chunk = (K + A.ksplit - 1) / A.ksplit;
@@ -538,6 +565,71 @@ __global__ void __launch_bounds__(512) batched_far_fp32_kernel(BatchArgs A, long
     double* C = A.far + ((((size_t)q * A.n_tiles + tile) * 2 + 1) * B + i0 + r) * ld + lane * D;
 #pragma unroll
     for (int c = 0; c < D; ++c) { P[c] = dP[r][c]; C[c] = dC[r][c]; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Far kernels for order groups whose components have different orders
+// (non-commensurate systems): the same sums with component c's weights on
+// column lane * D + c, one component after another (lane = trajectory).
+// FP64, or FP32 operands with FP32 sums within KB-row blocks (KB = 0: FP64).
+// ---------------------------------------------------------------------------
+template <int D, int B, int KB>
+__global__ void __launch_bounds__(256) batched_far_percomp_kernel(BatchArgs A, long long s) {
+  constexpr int R = B / 8;
+  constexpr int ld = kTrajPerTile * D;
+  using real = typename std::conditional<KB == 0, double, float>::type;
+  const int tile = blockIdx.x, q = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TileDesc& T = A.tiles[tile];
+  const long long K = s - A.far_k0;
+  const long long chunk = (K + A.ksplit - 1) / A.ksplit;
+  const long long kb = A.far_k0 + (long long)q * chunk, ke = min(s, kb + chunk);
+  const long long blk = KB == 0 ? (ke > kb ? ke - kb : 1) : KB;
+  const int i0 = warp * R;
+  for (int c = 0; c < D; ++c) {
+    const real* __restrict__ wb;
+    const real* __restrict__ wa;
+    const real* __restrict__ F;
+    if constexpr (KB == 0) {
+      wb = A.bucket_b[T.bucket * kMaxD + c];
+      wa = A.bucket_a[T.bucket * kMaxD + c];
+      F = A.F + T.f_off;
+    } else {
+      wb = A.bucket_b32[T.bucket * kMaxD + c];
+      wa = A.bucket_a32[T.bucket * kMaxD + c];
+      F = A.F32 + T.f_off;
+    }
+    double dP[R], dC[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dP[r] = dC[r] = 0.0;
+    for (long long k0 = kb; k0 < ke; k0 += blk) {
+      const long long k1 = min(ke, k0 + blk);
+      real accP[R], accC[R], wbv[R], wav[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        accP[r] = accC[r] = (real)0;
+        wbv[r] = wb[s + i0 + r - k0];
+        wav[r] = wa[s + i0 + r - k0];
+      }
+      for (long long k = k0; k < k1; ++k) {
+        const real f = F[k * ld + lane * D + c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          accP[r] = fma(wbv[r], f, accP[r]);
+          accC[r] = fma(wav[r], f, accC[r]);
+        }
+#pragma unroll
+        for (int r = R - 1; r > 0; --r) { wbv[r] = wbv[r - 1]; wav[r] = wav[r - 1]; }
+        if (k + 1 < k1) { wbv[0] = wb[s + i0 - (k + 1)]; wav[0] = wa[s + i0 - (k + 1)]; }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) { dP[r] += (double)accP[r]; dC[r] += (double)accC[r]; }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      A.far[((((size_t)q * A.n_tiles + tile) * 2 + 0) * B + i0 + r) * ld + lane * D + c] = dP[r];
+      A.far[((((size_t)q * A.n_tiles + tile) * 2 + 1) * B + i0 + r) * ld + lane * D + c] = dC[r];
+    }
   }
 }
 
@@ -605,6 +697,17 @@ cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long 
 cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, int n_active, long long s,
                                cudaStream_t st) {
   dim3 grid(n_active, A.ksplit);
+  if (A.per_comp) {
+    if (A.B != 64) return cudaErrorInvalidValue;
+    if (prec == ABM_PREC_FP64) {
+      if (d == 3) batched_far_percomp_kernel<3, 64, 0><<<grid, 256, 0, st>>>(A, s);
+      else batched_far_percomp_kernel<1, 64, 0><<<grid, 256, 0, st>>>(A, s);
+    } else {
+      if (d == 3) batched_far_percomp_kernel<3, 64, 512><<<grid, 256, 0, st>>>(A, s);
+      else batched_far_percomp_kernel<1, 64, 512><<<grid, 256, 0, st>>>(A, s);
+    }
+    return cudaGetLastError();
+  }
   if (prec == ABM_PREC_FP64) {
     if (A.B != 64) return cudaErrorInvalidValue;
     if (d == 3) batched_far_fp64_kernel<3, 64><<<grid, 256, 0, st>>>(A, s);

@@ -25,7 +25,10 @@ struct BatchArgs {
   int ksplit;              // history split of the far kernel
   int far_k0;              // first history row of the far sums: 1 forward (row 0 = the
                            // j = 0 term, kept in FP64), 0 adjoint
-  // per alpha group
+  int per_comp;            // 1: some group's orders differ per component (the SIMT far
+                           // kernels then take one weight set per component)
+  // per order group (trajectories with the same orders) and state component:
+  // entry [group * kMaxD + component]
   const double* bucket_alpha;
   const double* const* bucket_b;
   const double* const* bucket_a;
@@ -33,12 +36,14 @@ struct BatchArgs {
   const float* const* bucket_b32;
   const float* const* bucket_a32;
   const double* bucket_g;
+  const int* bucket_taylor;  // per group: bit c = component c has order above one
   // per trajectory (device)
   const double* h;
   const int* N;
   const double* params;
   const double* y0;
-  double* hhat;
+  const double* y0d;       // initial derivatives [M][D] (orders above one) or null
+  double* hhat;            // h^alpha per trajectory and component, [M][kMaxD]
   // histories
   double* F;               // FP64, per tile [rows][32*D]
   float* F32;              // FP32 shadow or null
@@ -77,6 +82,8 @@ struct AdjArgs {
   const TileDesc* tiles;   // forward column tiles (sorted by n_tile descending)
   const TileDesc* atiles;  // adjoint tiles: 2t = mu~ history, 2t+1 = lambda~ history
   int B;
+  // tables as in BatchArgs ([group * kMaxD + component]); the adjoint takes
+  // commensurate orders and reads component 0
   const double* bucket_alpha;
   const double* const* bucket_b;
   const double* const* bucket_a;
@@ -86,7 +93,7 @@ struct AdjArgs {
   const int* N;
   const double* params;
   const double* y0;
-  double* hhat;
+  double* hhat;            // [M][kMaxD], component 0 used
   const double* Y;
   const double* YP;
   const double* G;

@@ -57,6 +57,7 @@ __device__ __forceinline__ double sum_parts(const double* p, int ks, size_t stri
 struct TrajParams {
   double p[kMaxParams];
   double y0[kMaxD];
+  double y0d[kMaxD];  // initial derivatives y'(0), used by components of order above one
 };
 
 }  // namespace abm

@@ -24,15 +24,19 @@ struct PersistArgs {
   double* F;                   // (N+1) x D history, FP64
   double* Y;                   // (N+1) x D
   double* YP;                  // (N+1) x D or null
-  const double* b;
-  const double* a;
-  const double* c;
-  const double* g;             // 1/Gamma(alpha+2)
+  // weights per state component (all equal for a commensurate order): b_m,
+  // a_m, c_m over lags 0..N+2B+1 and g = 1/Gamma(alpha+2)
+  const double* b[kMaxD];
+  const double* a[kMaxD];
+  const double* c[kMaxD];
+  const double* g[kMaxD];
   double* partial;             // [kPersistRing][grid-1][kPersistB][2D]
   unsigned long long* flags;   // [0] rows_done, [1..kPersistRing] far counts; zero at launch
   unsigned long long* status;
   TrajParams tp;
-  double alpha, h;
+  double alpha[kMaxD];         // order per component (alpha[0] also enters the manufactured f)
+  double h;
+  int taylor_mask;             // bit c: component c has order above one (y'(0) t in its Taylor sum)
   int N;
   long long spin_budget;       // clock64 cycles per wait
   int withhold_tile;           // testing: far CTAs never count this tile (-1 = off)
@@ -40,7 +44,8 @@ struct PersistArgs {
 };
 
 cudaError_t launch_far_single(int d, const FarSingleArgs& A, int B, int grid, cudaStream_t st);
-cudaError_t launch_persistent(int sys, const PersistArgs& A, int grid, cudaStream_t st);
+// nc = 1: one weight set for every component; nc = d: one per component.
+cudaError_t launch_persistent(int sys, int nc, const PersistArgs& A, int grid, cudaStream_t st);
 int persistent_max_grid(int sys);
 size_t persistent_smem_bytes();
 

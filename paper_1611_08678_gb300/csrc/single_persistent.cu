@@ -67,15 +67,17 @@ __device__ __forceinline__ void named_bar(int id, int count) {
 // Sums over history rows [c0, c1) for targets s..s+B-1 of
 //   b_{s+i-k} F[k][c] and a_{s+i-k} F[k][c];  writes B x 2D values to out.
 // NT threads: each owns R consecutive targets over a contiguous sub-range of
-// rows, the Toeplitz weights kept as a sliding register window.  F is read
-// through L2 (ld.global.cg): rows next to the ones read may be written by
-// another SM later in the same launch.
-template <int D, int B, int R, int NT>
-__device__ void far_chunk(const double* __restrict__ F, const double* __restrict__ b,
-                          const double* __restrict__ a, long long s, long long c0, long long c1,
-                          double* red, double* out) {
+// rows, the Toeplitz weights kept as a sliding register window.  NC = 1: one
+// weight vector for every component; NC = D: component c uses b[c], a[c]
+// (orders that differ per component).  F is read through L2
+// (ld.global.cg): rows next to the ones read may be written by another SM
+// later in the same launch.
+template <int D, int B, int R, int NT, int NC>
+__device__ void far_chunk(const double* __restrict__ F, const double* const* bv, const double* const* av,
+                          long long s, long long c0, long long c1, double* red, double* out) {
   constexpr int RG = B / R, KL = NT / RG, V = 2 * D;
   static_assert(RG * KL == NT, "thread layout");
+  static_assert(NC == 1 || NC == D, "weight sets");
   const int tid = threadIdx.x, rg = tid % RG, kl = tid / RG, i0 = rg * R;
   const long long len = c1 > c0 ? c1 - c0 : 0;
   const long long sub = (len + KL - 1) / KL;
@@ -86,12 +88,18 @@ __device__ void far_chunk(const double* __restrict__ F, const double* __restrict
 #pragma unroll
     for (int c = 0; c < D; ++c) accP[r][c] = accC[r][c] = 0.0;
   if (kb < ke) {
-    double wb[R], wa[R];
+    const double* b[NC];
+    const double* a[NC];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      wb[r] = __ldg(b + (s + i0 + r - kb));
-      wa[r] = __ldg(a + (s + i0 + r - kb));
-    }
+    for (int w = 0; w < NC; ++w) { b[w] = bv[w]; a[w] = av[w]; }
+    double wb[R][NC], wa[R][NC];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int w = 0; w < NC; ++w) {
+        wb[r][w] = __ldg(b[w] + (s + i0 + r - kb));
+        wa[r][w] = __ldg(a[w] + (s + i0 + r - kb));
+      }
     for (long long k = kb; k < ke; ++k) {
       double f[D];
 #pragma unroll
@@ -100,14 +108,19 @@ __device__ void far_chunk(const double* __restrict__ F, const double* __restrict
       for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          accP[r][c] = fma(wb[r], f[c], accP[r][c]);
-          accC[r][c] = fma(wa[r], f[c], accC[r][c]);
+          accP[r][c] = fma(wb[r][NC == 1 ? 0 : c], f[c], accP[r][c]);
+          accC[r][c] = fma(wa[r][NC == 1 ? 0 : c], f[c], accC[r][c]);
         }
 #pragma unroll
-      for (int r = R - 1; r > 0; --r) { wb[r] = wb[r - 1]; wa[r] = wa[r - 1]; }
+      for (int r = R - 1; r > 0; --r)
+#pragma unroll
+        for (int w = 0; w < NC; ++w) { wb[r][w] = wb[r - 1][w]; wa[r][w] = wa[r - 1][w]; }
       if (k + 1 < ke) {
-        wb[0] = __ldg(b + (s + i0 - (k + 1)));
-        wa[0] = __ldg(a + (s + i0 - (k + 1)));
+#pragma unroll
+        for (int w = 0; w < NC; ++w) {
+          wb[0][w] = __ldg(b[w] + (s + i0 - (k + 1)));
+          wa[0][w] = __ldg(a[w] + (s + i0 - (k + 1)));
+        }
       }
     }
   }
@@ -128,10 +141,11 @@ __device__ void far_chunk(const double* __restrict__ F, const double* __restrict
   __syncthreads();
 }
 
-template <int SYS>
+template <int SYS, int NC>
 __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A) {
   using S = Sys<SYS>;
   constexpr int D = S::D, V = 2 * D;
+  constexpr int WL = 2 * PB + 1;  // near lags kept in shared memory per weight set
   extern __shared__ __align__(16) double dyn[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int W = gridDim.x - 1;  // far CTAs
@@ -151,7 +165,7 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
       if (!ok_s) return;
       const long long K = e - 1, chunk = (K + W - 1) / W;
       const long long c0 = 1 + (long long)w * chunk, c1 = min(e, c0 + chunk);
-      far_chunk<D, PB, 4, PT>(A.F, A.b, A.a, s, c0, c1, dyn,
+      far_chunk<D, PB, 4, PT, NC>(A.F, A.b, A.a, s, c0, c1, dyn,
                               A.partial + ((size_t)(j % PR) * W + w) * (PB * V));
       __threadfence();
       __syncthreads();
@@ -162,24 +176,27 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
 
   // -------------------------------- near role --------------------------------
   double* farv = dyn;                    // [PB * V]
-  double* wsb = farv + PB * V;           // lags 0..2PB
-  double* wsa = wsb + (2 * PB + 1);
+  double* wsb = farv + PB * V;           // [NC][lags 0..2PB]
+  double* wsa = wsb + NC * WL;
   __shared__ double Fs[4][kMaxD];        // ring of the last f rows
   __shared__ double accn[2][8];          // sums handed from the scatter warp to the chain
-  __shared__ double ysh[kMaxD], ysh2[kMaxD], F0s[kMaxD], consts[2];
+  __shared__ double ysh[kMaxD], ysh2[kMaxD], F0s[kMaxD], hhs[kMaxD], gs[kMaxD];
 
   const double* p = A.tp.p;
-  for (int m = tid; m <= 2 * PB; m += PT) { wsb[m] = A.b[m]; wsa[m] = A.a[m]; }
-  if (tid == 0) {
-    consts[0] = pow(A.h, A.alpha);
-    consts[1] = *A.g;
+  for (int m = tid; m < NC * WL; m += PT) {
+    wsb[m] = A.b[m / WL][m % WL];
+    wsa[m] = A.a[m / WL][m % WL];
+  }
+  if (tid < NC) {
+    hhs[tid] = pow(A.h, A.alpha[tid]);
+    gs[tid] = *A.g[tid];
   }
   if (warp < D && lane == 0) {
     const int c = warp;
     double y0v[D];
 #pragma unroll
     for (int q = 0; q < D; ++q) y0v[q] = A.tp.y0[q];
-    const double f0 = S::fc(c, p, A.alpha, 0.0, y0v);
+    const double f0 = S::fc(c, p, A.alpha[0], 0.0, y0v);
     F0s[c] = f0;
     Fs[0][c] = f0;
     A.F[c] = f0;
@@ -187,7 +204,7 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
     if (A.YP) A.YP[c] = A.tp.y0[c];
   }
   __syncthreads();
-  const double hh = consts[0], g = consts[1], h = A.h;
+  const double h = A.h;
 
   // scatter-warp registers: sums for targets of this tile (cur) and the next
   double sPc[D], sCc[D], sPn[D], sCn[D];
@@ -224,11 +241,11 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
         sPn[q] = 0.0; sCn[q] = 0.0;
       }
       if (lane < nb) {
-        const double bm = A.b[m], cm = A.c[m];
 #pragma unroll
         for (int q = 0; q < D; ++q) {
-          sPc[q] += fma(bm, F0s[q], farv[lane * V + q]);
-          sCc[q] += fma(cm, F0s[q], farv[lane * V + D + q]);
+          const int w = NC == 1 ? 0 : q;
+          sPc[q] += fma(A.b[w][m], F0s[q], farv[lane * V + q]);
+          sCc[q] += fma(A.c[w][m], F0s[q], farv[lane * V + D + q]);
         }
       }
       if (lane == 0) {
@@ -244,14 +261,22 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
         const int par = i & 1;
         if (warp < D) {
           const int c = warp;
+          const int wc = NC == 1 ? 0 : c;
+          const double hh = hhs[wc], g = gs[wc];
           const double t1 = (double)(n + 1) * h;
-          double y0c = A.tp.y0[0];
+          double y0c = A.tp.y0[0], y0dc = A.tp.y0d[0];
 #pragma unroll
-          for (int q = 1; q < D; ++q) y0c = (c == q) ? A.tp.y0[q] : y0c;
+          for (int q = 1; q < D; ++q) {
+            y0c = (c == q) ? A.tp.y0[q] : y0c;
+            y0dc = (c == q) ? A.tp.y0d[q] : y0dc;
+          }
+          // Taylor sum of the initial values (eq. 2): y0, plus t y'(0) for an
+          // order above one
+          if ((A.taylor_mask >> c) & 1) y0c = fma(t1, y0dc, y0c);
           double v = 0.0;
           if (lane < 2) {
             v = accn[par][lane == 0 ? c : D + c];
-            if (n >= 1) v = fma(lane == 0 ? wsb[0] : wsa[0], Fs[n & 3][c], v);
+            if (n >= 1) v = fma(lane == 0 ? wsb[wc * WL] : wsa[wc * WL], Fs[n & 3][c], v);
           }
           const double vc = __shfl_sync(0xffffffffu, v, 1);
           const double yp = fma(hh, v, y0c);
@@ -260,7 +285,7 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
           double ypv[D];
 #pragma unroll
           for (int q = 0; q < D; ++q) ypv[q] = ysh[q];
-          const double fp = S::fc(c, p, A.alpha, t1, ypv);
+          const double fp = S::fc(c, p, A.alpha[0], t1, ypv);
           double y = fma(hh, fma(g, fp, vc), y0c);
           if (lane == 0) ysh2[c] = y;
           named_bar(2, 32 * D);
@@ -271,7 +296,7 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
           // pass's state; the exchange alternates between ysh and ysh2 (every
           // warp read the other one before the barrier it just passed)
           for (int it = 1; it < A.passes; ++it) {
-            const double fq = S::fc(c, p, A.alpha, t1, yv);
+            const double fq = S::fc(c, p, A.alpha[0], t1, yv);
             y = fma(hh, fma(g, fq, vc), y0c);
             double* xb = (it & 1) ? ysh : ysh2;
             if (lane == 0) xb[c] = y;
@@ -279,7 +304,7 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
 #pragma unroll
             for (int q = 0; q < D; ++q) yv[q] = xb[q];
           }
-          const double fy = S::fc(c, p, A.alpha, t1, yv);
+          const double fy = S::fc(c, p, A.alpha[0], t1, yv);
           if (lane == 0) {
             Fs[(n + 1) & 3][c] = fy;
             A.F[(n + 1) * D + c] = fy;
@@ -294,14 +319,20 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
             for (int q = 0; q < D; ++q) fn[q] = Fs[n & 3][q];
             const long long lagc = s + lane - n;       // target s+lane of this tile
             if (lagc > 0) {
-              const double wb = wsb[lagc], wa = wsa[lagc];
 #pragma unroll
-              for (int q = 0; q < D; ++q) { sPc[q] = fma(wb, fn[q], sPc[q]); sCc[q] = fma(wa, fn[q], sCc[q]); }
+              for (int q = 0; q < D; ++q) {
+                const int w = (NC == 1 ? 0 : q) * WL;
+                sPc[q] = fma(wsb[w + lagc], fn[q], sPc[q]);
+                sCc[q] = fma(wsa[w + lagc], fn[q], sCc[q]);
+              }
             }
             const long long lagn = s + PB + lane - n;  // target s+PB+lane of the next tile, >= 1
-            const double wb = wsb[lagn], wa = wsa[lagn];
 #pragma unroll
-            for (int q = 0; q < D; ++q) { sPn[q] = fma(wb, fn[q], sPn[q]); sCn[q] = fma(wa, fn[q], sCn[q]); }
+            for (int q = 0; q < D; ++q) {
+              const int w = (NC == 1 ? 0 : q) * WL;
+              sPn[q] = fma(wsb[w + lagn], fn[q], sPn[q]);
+              sCn[q] = fma(wsa[w + lagn], fn[q], sCn[q]);
+            }
           }
           if (i + 1 < nb && lane == i + 1) {
 #pragma unroll
@@ -329,9 +360,9 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
 
 size_t persistent_smem_bytes() { return 116 * 1024; }
 
-template <int SYS>
+template <int SYS, int NC>
 cudaError_t launch_persistent_t(const PersistArgs& A, int grid, cudaStream_t st) {
-  auto fn = single_persistent_kernel<SYS>;
+  auto fn = single_persistent_kernel<SYS, NC>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)persistent_smem_bytes());
   if (e != cudaSuccess) return e;
@@ -340,9 +371,15 @@ cudaError_t launch_persistent_t(const PersistArgs& A, int grid, cudaStream_t st)
   return cudaLaunchCooperativeKernel((void*)fn, dim3(grid), dim3(PT), args, persistent_smem_bytes(), st);
 }
 
-cudaError_t launch_persistent(int sys, const PersistArgs& A, int grid, cudaStream_t st) {
+cudaError_t launch_persistent(int sys, int nc, const PersistArgs& A, int grid, cudaStream_t st) {
   cudaError_t err = cudaErrorInvalidValue;
-  ABM_DISPATCH_SYSTEM(sys, err = launch_persistent_t<SYS>(A, grid, st));
+  if (nc == 1) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_persistent_t<SYS, 1>(A, grid, st)));
+  } else {
+    ABM_DISPATCH_SYSTEM(sys, {
+      if (nc == Sys<SYS>::D) err = (launch_persistent_t<SYS, Sys<SYS>::D>(A, grid, st));
+    });
+  }
   return err;
 }
 
@@ -351,10 +388,18 @@ int persistent_max_grid(int sys) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   ABM_DISPATCH_SYSTEM(sys, {
-    cudaFuncSetAttribute(single_persistent_kernel<SYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(single_persistent_kernel<SYS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)persistent_smem_bytes());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, single_persistent_kernel<SYS>, PT,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, single_persistent_kernel<SYS, 1>, PT,
                                                   persistent_smem_bytes());
+    if (Sys<SYS>::D > 1) {  // the per-component kernel must fit as many CTAs
+      int b2 = 0;
+      cudaFuncSetAttribute(single_persistent_kernel<SYS, Sys<SYS>::D>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persistent_smem_bytes());
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, single_persistent_kernel<SYS, Sys<SYS>::D>, PT,
+                                                    persistent_smem_bytes());
+      blocks = b2 < blocks ? b2 : blocks;
+    }
   });
   return blocks * sms;
 }
@@ -473,21 +518,24 @@ extern "C" abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, 
   A.F = base + kOffF;
   A.Y = Y;
   A.YP = YP;
-  A.b = base + kOffB;
-  A.a = base + kOffA;
-  A.c = base + kOffC;
-  A.g = base + kOffG;
+  for (int c = 0; c < kMaxD; ++c) {
+    A.b[c] = base + kOffB;
+    A.a[c] = base + kOffA;
+    A.c[c] = base + kOffC;
+    A.g[c] = base + kOffG;
+    A.alpha[c] = alpha;
+  }
   A.partial = base + kOffPart;
   A.flags = reinterpret_cast<unsigned long long*>(flags_d);
   A.status = reinterpret_cast<unsigned long long*>(flags_d + 8);
   A.tp = tp;
-  A.alpha = alpha;
   A.h = h;
+  A.taylor_mask = 0;
   A.N = N;
   A.spin_budget = 4000000000LL;
   A.withhold_tile = -1;
   A.passes = 1;
-  if ((e = launch_persistent(sys, A, grid, st)) != cudaSuccess) return cuda_err(e, "persistent kernel");
+  if ((e = launch_persistent(sys, 1, A, grid, st)) != cudaSuccess) return cuda_err(e, "persistent kernel");
   unsigned long long w = 0;
   if ((e = cudaMemcpyAsync(&w, A.status, sizeof(w), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_err(e, "status read");
