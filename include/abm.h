@@ -263,6 +263,51 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
                        long long ldY, const double* dLdY, double* dparams, double* dy0,
                        void* stream);
 
+/* Checkpoint and resume.  Every step of the scheme reads the whole history
+ * (Sec. 2: y_{n+1} depends on f_0..f_n), so the state of a solve at step n is
+ * y(0), y'(0) and the f history f_0..f_n; the paper has no checkpointing.
+ *
+ * abm_history: copies f_0..f_{rows-1} of the last single-trajectory solve on
+ * this plan (abm_solve, abm_solve_ext or abm_solve_resume; rows <= its N+1)
+ * to F, rows x d doubles in host or device memory, enqueued on `stream`
+ * (page-locked host memory keeps the copy asynchronous). */
+abm_status abm_history(abm_plan p, int rows, double* F, void* stream);
+
+/* abm_solve_resume: continues a single-trajectory solve of the problem given
+ * by alpha (d orders), h, params, y0, y0d (as abm_solve_ext) from step n0 to
+ * step N (0 <= n0 <= N <= n_max): F holds f_0..f_n0 of the earlier solve
+ * ((n0+1) x d doubles, host or device, as abm_history wrote them; unused when
+ * n0 < 32).  Stepping restarts at the time tile (32 steps) that holds step
+ * n0 + 1: rows s..N of Y (and YP) are written, where s is n0 rounded down to
+ * a multiple of 32; rows s+1..n0 are recomputed with the arithmetic of an
+ * uninterrupted solve, so a solve split at any n0 and resumed equals the
+ * uninterrupted one bit for bit.  Rows 0..s-1 of Y are not touched. */
+abm_status abm_solve_resume(abm_plan p, const double* alpha, double h, int n0, int N, const double* params,
+                            const double* y0, const double* y0d, const double* F, double* Y, double* YP,
+                            void* stream);
+
+/* abm_history_batched: copies f_0..f_{min(rows, N[i]+1)-1} of every
+ * trajectory of the last batched solve on this plan into F, a DEVICE array
+ * M x ldF x d (ldF >= rows), row k of trajectory i at (i ldF + k) d.  The
+ * arguments alpha (M x d orders, the abm_solve_batched_ext convention), h and
+ * N must be those of that solve. */
+abm_status abm_history_batched(abm_plan p, int M, const double* alpha, const double* h, const int* N, int rows,
+                               double* F, long long ldF, void* stream);
+
+/* abm_solve_batched_resume: continues a batched solve (arguments as
+ * abm_solve_batched_ext) from step n0 (0 <= n0 <= N[i] for every i): F is a
+ * DEVICE array M x ldF x d (ldF >= n0+1) holding f_0..f_n0 of each
+ * trajectory, as abm_history_batched wrote them (unused when n0 < tile_B).
+ * Stepping restarts at the time tile (tile_B steps, 64 by default) that holds
+ * step n0 + 1: rows s+1..N[i] of Y (and YP) are written, s = n0 rounded down
+ * to a multiple of tile_B, rows s+1..n0 recomputed as an uninterrupted solve
+ * computes them.  With an FP64 plan the result equals the uninterrupted solve
+ * bit for bit; the tensor-core plans add K-split far sums with atomics, whose
+ * order (and last bit) varies from run to run.  Never captured in a graph. */
+abm_status abm_solve_batched_resume(abm_plan p, int M, const double* alpha, const double* h, const int* N, int n0,
+                                    const double* params, const double* y0, const double* y0d, const double* F,
+                                    long long ldF, double* Y, long long ldY, double* YP, void* stream);
+
 /* Far-history sums alone (the A2 contraction, exposed for parity tests and
  * roofline measurement).  F: device, rows x cols row-major FP64 history
  * (row k = f_k).  For targets n = s..s+B-1 and history rows k in [k_lo, k_hi)

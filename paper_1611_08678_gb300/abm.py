@@ -25,7 +25,8 @@ STATUS = {0: "ABM_OK", 1: "ABM_ERR_INVALID_ARG", 2: "ABM_ERR_CUDA", 3: "ABM_ERR_
 EXPORTS = ["abm_plan_opts_default", "abm_system_dim", "abm_system_nparams", "abm_plan_create",
            "abm_plan_destroy", "abm_plan_sync", "abm_last_error", "abm_weights", "abm_solve",
            "abm_solve_batched", "abm_solve_batched_host", "abm_adjoint", "abm_far_history", "abm_solve_noalloc",
-           "abm_plan_kernel_times", "abm_solve_ext", "abm_solve_batched_ext"]
+           "abm_plan_kernel_times", "abm_solve_ext", "abm_solve_batched_ext", "abm_history", "abm_solve_resume",
+           "abm_history_batched", "abm_solve_batched_resume"]
 KERNEL_KINDS = {"weights": 0, "far": 1, "near": 2, "single": 3, "adjoint": 4}
 
 
@@ -78,6 +79,10 @@ def load(path: str = LIB_PATH):
         lib.abm_solve_ext.argtypes = [_vp, _dp, D, I, _dp, _dp, _dp, _vp, _vp, _vp]
         lib.abm_solve_batched_ext.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_solve_batched_host.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
+        lib.abm_history.argtypes = [_vp, I, _vp, _vp]
+        lib.abm_solve_resume.argtypes = [_vp, _dp, D, I, I, _dp, _dp, _dp, _vp, _vp, _vp, _vp]
+        lib.abm_history_batched.argtypes = [_vp, I, _dp, _dp, _ip, I, _vp, LL, _vp]
+        lib.abm_solve_batched_resume.argtypes = [_vp, I, _dp, _dp, _ip, I, _vp, _vp, _vp, _vp, LL, _vp, LL, _vp, _vp]
         lib.abm_adjoint.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp, _vp, _vp]
         lib.abm_far_history.argtypes = [_vp, D, _vp, LL, LL, LL, I, LL, LL, _vp, _vp, _vp]
         lib.abm_plan_kernel_times.argtypes = [_vp, I, _vp, I, ctypes.POINTER(LL), ctypes.POINTER(D)]
@@ -262,6 +267,100 @@ class Plan:
         if sync:
             self.sync(stream)
         return (Y, YP) if want_yp or YP is not None else Y
+
+    # -- checkpoint / resume --
+    def history(self, rows, F=None, stream=None, sync=True):
+        """abm_history: f_0..f_{rows-1} of the last single-trajectory solve
+        (a CUDA tensor (rows, d), or F given: CUDA or host float64 tensor)."""
+        torch = _torch()
+        if F is None:
+            F = torch.empty(rows, self.d, dtype=torch.float64, device="cuda")
+        _check_out(F, (rows, self.d), "F", cuda=F.is_cuda)
+        self._check(self.lib.abm_history(self.h, int(rows), _dptr(F), _stream_ptr(stream)), "abm_history")
+        if sync:
+            self.sync(stream)
+        return F
+
+    def solve_resume(self, alpha, h, n0, N, params, y0, F, y0d=None, Y=None, YP=None, want_yp=False,
+                     stream=None, sync=True):
+        """abm_solve_resume: continue from step n0 to N with F = f_0..f_n0."""
+        torch = _torch()
+        al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (self.d,)))
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        y = np.ascontiguousarray(y0, dtype=np.float64)
+        yd = None if y0d is None else np.ascontiguousarray(y0d, dtype=np.float64)
+        if p.size != self.np or y.size != self.d or (yd is not None and yd.size != self.d):
+            raise ValueError("params / y0 / y0d have the wrong size for this system")
+        if not (torch.is_tensor(F) and F.dtype == torch.float64 and F.is_contiguous() and F.numel() >= (n0 + 1) * self.d):
+            raise ValueError("F must be a contiguous float64 tensor holding rows 0..n0")
+        if Y is None:
+            Y = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
+        if YP is None and want_yp:
+            YP = torch.empty(N + 1, self.d, dtype=torch.float64, device="cuda")
+        _check_out(Y, (N + 1, self.d), "Y", more_rows=True)
+        _check_out(YP, (N + 1, self.d), "YP", more_rows=True)
+        st = self.lib.abm_solve_resume(self.h, al.ctypes.data_as(_dp), float(h), int(n0), int(N),
+                                       p.ctypes.data_as(_dp), y.ctypes.data_as(_dp),
+                                       yd.ctypes.data_as(_dp) if yd is not None else None, _dptr(F), _dptr(Y),
+                                       _dptr(YP), _stream_ptr(stream))
+        self._check(st, "abm_solve_resume")
+        if sync:
+            self.sync(stream)
+        return (Y, YP) if want_yp or YP is not None else Y
+
+    def _orders(self, alpha, M):
+        al = np.asarray(alpha, dtype=np.float64)
+        return np.ascontiguousarray(np.broadcast_to(al.reshape(M, -1), (M, self.d)))
+
+    def history_batched(self, alpha, h, N, rows, F=None, ldF=None, stream=None, sync=True):
+        """abm_history_batched: (M, ldF, d) CUDA tensor with f_0..f_min(rows, N_i+1)-1
+        of every trajectory of the last batched solve (same alpha, h, N)."""
+        torch = _torch()
+        hh = np.ascontiguousarray(h, dtype=np.float64)
+        NN = np.ascontiguousarray(N, dtype=np.int32)
+        M = NN.size
+        al = self._orders(alpha, M)
+        ldF = int(ldF or rows)
+        if F is None:
+            F = torch.zeros(M, ldF, self.d, dtype=torch.float64, device="cuda")
+        _check_out(F, (M, ldF, self.d), "F")
+        st = self.lib.abm_history_batched(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
+                                          NN.ctypes.data_as(_ip), int(rows), _dptr(F), ldF, _stream_ptr(stream))
+        self._check(st, "abm_history_batched")
+        if sync:
+            self.sync(stream)
+        return F
+
+    def solve_batched_resume(self, alpha, h, N, n0, params, y0, F, y0d=None, Y=None, YP=None, ldY=None,
+                             stream=None, sync=True):
+        """abm_solve_batched_resume: continue every trajectory from step n0
+        (F: (M, ldF, d) CUDA tensor of f_0..f_n0)."""
+        torch = _torch()
+        hh = np.ascontiguousarray(h, dtype=np.float64)
+        NN = np.ascontiguousarray(N, dtype=np.int32)
+        M = NN.size
+        al = self._orders(alpha, M)
+        params = _dev_f64(params, M * self.np, "params")
+        y0 = _dev_f64(y0, M * self.d, "y0")
+        yd = None if y0d is None else _dev_f64(y0d, M * self.d, "y0d")
+        if not (torch.is_tensor(F) and F.is_cuda and F.dtype == torch.float64 and F.is_contiguous() and F.dim() == 3
+                and F.shape[0] == M and F.shape[2] == self.d):
+            raise ValueError("F must be a contiguous float64 CUDA tensor of shape (M, ldF, d)")
+        if ldY is None:
+            ldY = int(NN.max()) + 1
+        if Y is None:
+            Y = torch.zeros(M, ldY, self.d, dtype=torch.float64, device="cuda")
+        _check_out(Y, (M, ldY, self.d), "Y")
+        _check_out(YP, (M, ldY, self.d), "YP")
+        self._ext_inputs = yd
+        st = self.lib.abm_solve_batched_resume(self.h, M, al.ctypes.data_as(_dp), hh.ctypes.data_as(_dp),
+                                               NN.ctypes.data_as(_ip), int(n0), _dptr(params), _dptr(y0), _dptr(yd),
+                                               _dptr(F), int(F.shape[1]), _dptr(Y), int(ldY), _dptr(YP),
+                                               _stream_ptr(stream))
+        self._check(st, "abm_solve_batched_resume")
+        if sync:
+            self.sync(stream)
+        return Y
 
     # -- batched --
     def solve_batched_ext(self, alpha, h, N, params, y0, y0d=None, Y=None, YP=None, want_yp=False, ldY=None,

@@ -36,6 +36,10 @@ bool make_tmap_bf16(CUtensorMap* out, void* base, unsigned long long inner, unsi
 cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, long long plane, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* far, int ksplit, int n_tiles, double* P, double* C, cudaStream_t st);
 cudaError_t launch_adjoint_setup(int sys, const AdjArgs& A, int n_tiles, cudaStream_t st);
+cudaError_t launch_import_history(int d, const BatchArgs& A, int n_tiles, long long s0, const double* Fin,
+                                  long long ldF, cudaStream_t st);
+cudaError_t launch_export_history(int d, const BatchArgs& A, int n_tiles, long long rows, double* Fout, long long ldF,
+                                  cudaStream_t st);
 cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, int wpc,
                                 int split, cudaStream_t st);
 cudaError_t launch_adjoint_finish(int sys, const AdjArgs& A, int M, cudaStream_t st);
@@ -70,6 +74,7 @@ struct abm_plan_s {
   unsigned long long use_clock = 0;
   // single trajectory
   double* F1 = nullptr;             // (n_max + B + 1) x d
+  int last_single_rows = 0;         // N + 1 of the last single-trajectory solve (abm_history)
   double* far1 = nullptr;           // [2][B][2d]
   double* part1 = nullptr;          // [2][G][B][2d]
   unsigned int* tickets = nullptr;  // [2]
@@ -466,7 +471,8 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
   CK(launch_batched_setup(p->sys, A, S.n_tiles, st), "setup kernel");
   const int ntime = (S.nmax + B - 1) / B;
   int n_active = S.n_tiles;
-  for (int j = 0; j < ntime; ++j) {
+  const int j0 = (int)(A.resume_row / B);  // resume: rows 0..j0 B come from the imported history
+  for (int j = j0; j < ntime; ++j) {
     const long long s = (long long)j * B;
     while (n_active > 0 && tiles[n_active - 1].n_tile <= s) --n_active;
     if (n_active == 0) break;
@@ -776,8 +782,12 @@ namespace {
 // The single-trajectory solve behind abm_solve and abm_solve_ext: alpha holds
 // one order per component (in (0, 2]); y0d the initial derivatives (NULL:
 // zero), used by components of order above one.
+// n0 > 0 (resume): F_in holds f_0..f_n0 of an earlier solve of the same
+// problem (host or device memory); stepping restarts at the time tile that
+// holds step n0 + 1, whose start row s0 <= n0 comes from F_in.
 abm_status solve_single(abm_plan p, const char* who, const double* alpha, double h, int N, const double* params,
-                        const double* y0, const double* y0d, double* Y, double* YP, cudaStream_t st) {
+                        const double* y0, const double* y0d, double* Y, double* YP, cudaStream_t st,
+                        int n0 = 0, const double* F_in = nullptr) {
   TrajParams tp{};
   for (int i = 0; i < p->np; ++i) {
     if (!std::isfinite(params[i])) return fail(p, ABM_ERR_INVALID_ARG, std::string(who) + ": non-finite parameter");
@@ -832,10 +842,15 @@ abm_status solve_single(abm_plan p, const char* who, const double* alpha, double
   A.spin_budget = p->o.spin_timeout_cycles > 0 ? p->o.spin_timeout_cycles : 4000000000LL;
   A.withhold_tile = p->o.test_withhold_tile > 0 ? p->o.test_withhold_tile - 1 : -1;
   A.passes = p->o.corrector_passes > 1 ? p->o.corrector_passes : 1;
+  A.start_tile = n0 / kPersistB;
+  if (A.start_tile > 0)
+    CK(cudaMemcpyAsync(p->F1, F_in, (size_t)(A.start_tile * kPersistB + 1) * p->d * sizeof(double),
+                       cudaMemcpyDefault, st), "history import");
   {
     Trace tr(p, ABM_KERNEL_SINGLE, st);
     CK(launch_persistent(p->sys, nc, A, p->Gp, st), "persistent single-trajectory kernel");
   }
+  p->last_single_rows = N + 1;
   return ABM_OK;
 }
 
@@ -862,6 +877,30 @@ abm_status abm_solve_ext(abm_plan p, const double* alpha, double h, int N, const
   for (int i = 0; i < p->d; ++i)
     if (!order_ok(alpha[i])) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_ext: every order must be in (0, 2]");
   return solve_single(p, "abm_solve_ext", alpha, h, N, params, y0, y0d, Y, YP, (cudaStream_t)stream);
+}
+
+abm_status abm_history(abm_plan p, int rows, double* F, void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (!F || rows < 1 || rows > p->last_single_rows)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_history: need 1 <= rows <= N+1 of the last single-trajectory solve "
+                                        "and a non-null F");
+  CK(cudaMemcpyAsync(F, p->F1, (size_t)rows * p->d * sizeof(double), cudaMemcpyDefault, (cudaStream_t)stream),
+     "history export");
+  return ABM_OK;
+}
+
+abm_status abm_solve_resume(abm_plan p, const double* alpha, double h, int n0, int N, const double* params,
+                            const double* y0, const double* y0d, const double* F, double* Y, double* YP,
+                            void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (!alpha || !(std::isfinite(h) && h > 0.0) || N < 1 || N > p->o.n_max || n0 < 0 || n0 > N || !params || !y0 ||
+      !Y || (n0 >= kPersistB && !F))
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_resume: need finite h > 0, 0 <= n0 <= N <= n_max, "
+                                        "non-null alpha/params/y0/Y and the history F");
+  for (int i = 0; i < p->d; ++i)
+    if (!order_ok(alpha[i])) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_resume: every order must be in (0, 2]");
+  if (n0 == N) return ABM_OK;
+  return solve_single(p, "abm_solve_resume", alpha, h, N, params, y0, y0d, Y, YP, (cudaStream_t)stream, n0, F);
 }
 
 }  // extern "C"
@@ -940,6 +979,45 @@ abm_status abm_solve_batched_ext(abm_plan p, int M, const double* alpha, const d
     return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched_ext: need 1 <= M <= max_batch and non-null arrays");
   return solve_batched_impl(p, "abm_solve_batched_ext", M, alpha, p->d, 2.0, h, N, params, y0, y0d, Y, ldY, YP,
                             (cudaStream_t)stream);
+}
+
+abm_status abm_history_batched(abm_plan p, int M, const double* alpha, const double* h, const int* N, int rows,
+                               double* F, long long ldF, void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !F || rows < 1 || ldF < rows)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_history_batched: need 1 <= M <= max_batch, rows >= 1, ldF >= rows "
+                                        "and non-null arrays");
+  cudaStream_t st = (cudaStream_t)stream;
+  int nmax = 0;  // the output has no ldY: the schedule is checked against the longest trajectory
+  for (int i = 0; i < M; ++i) nmax = std::max(nmax, N[i]);
+  Sched S;
+  abm_status rs = schedule_batch(p, M, alpha, p->d, 2.0, h, N, (long long)nmax + 1, st, S, "abm_history_batched");
+  if (rs) return rs;
+  const BatchArgs A = batch_args(p, S, nullptr, nullptr, nullptr, nullptr, nullptr, S.nmax + 1);
+  CK(launch_export_history(p->d, A, S.n_tiles, std::min<long long>(rows, (long long)S.nmax + 1), F, ldF, st),
+     "history export kernel");
+  return ABM_OK;
+}
+
+abm_status abm_solve_batched_resume(abm_plan p, int M, const double* alpha, const double* h, const int* N, int n0,
+                                    const double* params, const double* y0, const double* y0d, const double* F,
+                                    long long ldF, double* Y, long long ldY, double* YP, void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (M < 1 || M > p->o.max_batch || !alpha || !h || !N || !params || !y0 || !Y || n0 < 0 ||
+      (n0 >= p->B && (!F || ldF < (long long)n0 + 1)))
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched_resume: need 1 <= M <= max_batch, n0 >= 0, the history F "
+                                        "with ldF >= n0 + 1 and non-null arrays");
+  for (int i = 0; i < M; ++i)
+    if (N[i] < n0) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_batched_resume: every N[i] must be >= n0");
+  cudaStream_t st = (cudaStream_t)stream;
+  Sched S;
+  abm_status rs = schedule_batch(p, M, alpha, p->d, 2.0, h, N, ldY, st, S, "abm_solve_batched_resume");
+  if (rs) return rs;
+  BatchArgs A = batch_args(p, S, params, y0, y0d, Y, YP, ldY);
+  A.resume_row = (long long)(n0 / p->B) * p->B;
+  if (A.resume_row > 0)
+    CK(launch_import_history(p->d, A, S.n_tiles, A.resume_row, F, ldF, st), "history import kernel");
+  return enqueue_batched(p, S, A, st);
 }
 
 abm_status abm_solve_batched_host(abm_plan p, int M, const double* alpha, const double* h, const int* N,

@@ -39,6 +39,11 @@ __global__ void batched_setup_kernel(BatchArgs A) {
   for (int q = 0; q < S::NP; ++q) p[q] = A.params[(size_t)src * S::NP + q];
 #pragma unroll
   for (int c = 0; c < D; ++c) y0[c] = A.y0[(size_t)src * D + c];
+  if (traj >= 0) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) A.hhat[(size_t)traj * kMaxD + c] = pow(A.h[traj], A.bucket_alpha[bk + c]);
+  }
+  if (A.resume_row > 0) return;  // f_0 was imported with the history; Y row 0 is the caller's
   S::f(p, alpha, 0.0, y0, f0);
   double* F = A.F + T.f_off;
 #pragma unroll
@@ -49,8 +54,6 @@ __global__ void batched_setup_kernel(BatchArgs A) {
     for (int c = 0; c < D; ++c) F32[lane * D + c] = (float)f0[c];
   }
   if (traj >= 0) {
-#pragma unroll
-    for (int c = 0; c < D; ++c) A.hhat[(size_t)traj * kMaxD + c] = pow(A.h[traj], A.bucket_alpha[bk + c]);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       A.Y[(size_t)traj * A.ldY * D + c] = y0[c];

@@ -59,6 +59,8 @@ struct BatchArgs {
   long long ldY;
   unsigned long long* status;
   int passes;              // corrector passes per step (1 = PECE)
+  long long resume_row;    // resume: history rows 0..resume_row were imported and Y rows up
+                           // to it are the caller's (0 = a fresh solve)
 };
 
 // Arguments of the tensor-core far kernel (far_tc.cu).

@@ -41,6 +41,8 @@ struct PersistArgs {
   long long spin_budget;       // clock64 cycles per wait
   int withhold_tile;           // testing: far CTAs never count this tile (-1 = off)
   int passes;                  // corrector passes per step (1 = PECE)
+  int start_tile;              // resume: first time tile stepped; F rows 0..start_tile*B hold
+                               // the history of an earlier solve (0 = a fresh solve)
 };
 
 cudaError_t launch_far_single(int d, const FarSingleArgs& A, int B, int grid, cudaStream_t st);

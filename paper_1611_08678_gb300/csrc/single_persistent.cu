@@ -155,10 +155,12 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
   unsigned long long* far_count = A.flags + 1;  // [PR]
   __shared__ int ok_s;
 
+  const int j0 = A.start_tile;          // first tile stepped (resume)
+  const int jfar = j0 > 2 ? j0 : 2;      // first tile with far sums computed here
   if (blockIdx.x > 0) {
     // ------------------------------ far role ------------------------------
     const int w = blockIdx.x - 1;
-    for (int j = 2; j < ntiles; ++j) {
+    for (int j = jfar; j < ntiles; ++j) {
       const long long s = (long long)j * PB, e = (long long)(j - 1) * PB;
       if (tid == 0) ok_s = spin_geq(rows_done, (unsigned long long)e, A.status, A.spin_budget, kSiteSingleFar, j);
       __syncthreads();
@@ -191,17 +193,31 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
     hhs[tid] = pow(A.h, A.alpha[tid]);
     gs[tid] = *A.g[tid];
   }
-  if (warp < D && lane == 0) {
-    const int c = warp;
-    double y0v[D];
+  if (j0 == 0) {
+    if (warp < D && lane == 0) {
+      const int c = warp;
+      double y0v[D];
 #pragma unroll
-    for (int q = 0; q < D; ++q) y0v[q] = A.tp.y0[q];
-    const double f0 = S::fc(c, p, A.alpha[0], 0.0, y0v);
-    F0s[c] = f0;
-    Fs[0][c] = f0;
-    A.F[c] = f0;
-    A.Y[c] = A.tp.y0[c];
-    if (A.YP) A.YP[c] = A.tp.y0[c];
+      for (int q = 0; q < D; ++q) y0v[q] = A.tp.y0[q];
+      const double f0 = S::fc(c, p, A.alpha[0], 0.0, y0v);
+      F0s[c] = f0;
+      Fs[0][c] = f0;
+      A.F[c] = f0;
+      A.Y[c] = A.tp.y0[c];
+      if (A.YP) A.YP[c] = A.tp.y0[c];
+    }
+  } else {
+    // resume at row s0 = j0 B: f_0 and the ring of the last rows from the
+    // imported history; rows s0 + 1 and beyond are stepped below
+    const long long s0 = (long long)j0 * PB;
+    if (tid < D) {
+      F0s[tid] = A.F[tid];
+      for (long long n = s0 - 3 > 0 ? s0 - 3 : 0; n <= s0; ++n) Fs[n & 3][tid] = A.F[n * D + tid];
+    }
+    if (tid == 0) {  // rows 0..s0 are final: the far CTAs may start
+      dev_atomic rd(*rows_done);
+      rd.store((unsigned long long)(s0 + 1), cuda::memory_order_release);
+    }
   }
   __syncthreads();
   const double h = A.h;
@@ -210,14 +226,31 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
   double sPc[D], sCc[D], sPn[D], sCn[D];
 #pragma unroll
   for (int q = 0; q < D; ++q) sPc[q] = sCc[q] = sPn[q] = sCn[q] = 0.0;
+  if (j0 > 0 && warp == 3) {
+    // resume: the next-tile sums tile j0 - 1 would have handed over - rows of
+    // tile j0 - 1 weighted for the targets of tile j0, added in row order with
+    // the same operations as in the stepping loop below
+    const long long sp = (long long)(j0 - 1) * PB;
+    for (long long n = sp > 1 ? sp : 1; n < sp + PB; ++n) {
+      const long long lagn = sp + PB + lane - n;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const int w = (NC == 1 ? 0 : q) * WL;
+        const double fq = A.F[n * D + q];
+        sPn[q] = fma(wsb[w + lagn], fq, sPn[q]);
+        sCn[q] = fma(wsa[w + lagn], fq, sCn[q]);
+      }
+    }
+  }
 
-  for (int j = 0; j < ntiles; ++j) {
+  for (int j = j0; j < ntiles; ++j) {
     const long long s = (long long)j * PB;
     const int nb = (int)min((long long)PB, (long long)N - s);
     // ---- far sums of this tile: fixed-order sum of the W partials ----
     if (j >= 2) {
       if (tid == 0) {
-        const unsigned long long target = (unsigned long long)W * (unsigned long long)((j - 2) / PR + 1);
+        // far CTAs have counted every tile from jfar on in its slot j % PR
+        const unsigned long long target = (unsigned long long)W * (unsigned long long)((j - jfar) / PR + 1);
         ok_s = spin_geq(far_count + (j % PR), target, A.status, A.spin_budget, kSiteSingleNear, j);
       }
       __syncthreads();
@@ -535,6 +568,7 @@ extern "C" abm_status abm_solve_noalloc(abm_system sys, double alpha, double h, 
   A.spin_budget = 4000000000LL;
   A.withhold_tile = -1;
   A.passes = 1;
+  A.start_tile = 0;
   if ((e = launch_persistent(sys, 1, A, grid, st)) != cudaSuccess) return cuda_err(e, "persistent kernel");
   unsigned long long w = 0;
   if ((e = cudaMemcpyAsync(&w, A.status, sizeof(w), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
