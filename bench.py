@@ -517,7 +517,7 @@ def bench_batched(args, name, w, prec, world, rank, local):
     shard = w.subset(shard_indices(w.M, rank, world, w.N)) if world > 1 else w
     N = shard.N
     ldY = int(N.max()) + 1
-    tuned = {"near_warps": 0, "far_split": 0}
+    tuned = {"near_warps": 0, "far_split": 0, "near_split": 0}
     if tc_far(prec) and not args.no_tune:
         from paper_1611_08678_gb300 import autotune
         tuned = autotune.tune_batched(shard, prec)  # untimed; cached per shape
@@ -565,7 +565,8 @@ def bench_batched(args, name, w, prec, world, rank, local):
     # that give the roofline its kernel times
     plan.close()  # one workspace at a time
     gplan = abm.Plan(shard.system, n_max=int(N.max()), max_batch=shard.M, prec=prec, use_graph=True,
-                     corrector_passes=passes, near_warps=tuned["near_warps"], far_split=tuned["far_split"])
+                     corrector_passes=passes, near_warps=tuned["near_warps"], far_split=tuned["far_split"],
+                     near_split=tuned.get("near_split", 0))
     gsteps = max(1, min(args.steps, 3))
     for _ in range(2):  # capture, then one replay
         gplan.solve_batched(shard.alpha, shard.h, N, params, y0, Y=Y, ldY=ldY, sync=False, stream=stream)
@@ -591,12 +592,16 @@ def bench_batched(args, name, w, prec, world, rank, local):
                    "N_range": [int(w.N.min()), int(w.N.max())], "sum_N": int(w.N.sum()),
                    "alphas": sorted(set(float(a) for a in w.alpha)), "far_precision": prec,
                    "parallelism": f"trajectory shards x{world}",
-                   "tuned": {"near_warps": tuned["near_warps"], "far_split": tuned["far_split"],
-                             "cached": bool(tuned.get("cached", False))},
+                   "tuned": {"far_split": tuned["far_split"], "near_warps": tuned["near_warps"],
+                             "near_split": tuned.get("near_split", 0), "cached": bool(tuned.get("cached", False)),
+                             "timed_candidates": len(tuned.get("results", []))},
                    "l2": "inputs larger than L2 (f history of all trajectories, several GB)"},
         "history_mac_per_s": macs_all / total_max,
         "roofline": roof,
         "kernel_ms_per_solve": {k: v[1] / args.steps for k, v in times.items() if v[0]},
+        # device time per solve outside every kernel of the library (launch
+        # gaps between the ~2 launches per time tile), from the same events
+        "launch_gaps_ms_per_solve": total / args.steps * 1e3 - sum(v[1] for v in times.values()) / args.steps,
         "e2e": e2e,
         "graph_replay": graph,
         "gpu_launches": int(sum(v[0] for v in times.values())),

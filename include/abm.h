@@ -237,9 +237,11 @@ abm_status abm_solve_batched_ext(abm_plan p, int M, const double* alpha, const d
  * and trajectory i's rows 0..N[i] of Y (and YP when not NULL), laid out as in
  * abm_solve_batched with leading dimension ldY, are written to host memory;
  * the rest of Y is left untouched.  The inputs are copied up on `stream`
- * first.  Each trajectory's rows are copied down on a stream of the plan as
- * soon as the time tile that finishes it has run, overlapping the remaining
- * time tiles.  The call's work, copies included, is complete once `stream`
+ * first.  Rows are copied down on a stream of the plan while the remaining
+ * time tiles run: a trajectory's last rows right after the time tile that
+ * finishes it, and, whenever the still-running trajectories form at most 32
+ * runs of consecutive indices (always, when all N[i] are equal), their rows
+ * of each time tile right after that tile, as 2D copies.  The call's work, copies included, is complete once `stream`
  * has passed it (abm_plan_sync).  The host arrays must stay valid until then
  * and should be page-locked (cudaHostAlloc / cudaHostRegister): with pageable
  * memory the copies still happen but stop overlapping.  The first call

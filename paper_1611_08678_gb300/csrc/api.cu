@@ -448,17 +448,64 @@ abm_status schedule_batch(abm_plan p, int M, const double* alpha, int astride, d
   return ABM_OK;
 }
 
-// Copy-out of finished trajectories to host memory while later time tiles
-// run (abm_solve_batched_host): by_tile[j] lists the trajectories whose last
-// row N_i is written by the near kernel of time tile j.
+// Copy-out of finished rows to host memory while later time tiles run
+// (abm_solve_batched_host).  ops[j] lists the copies issued behind time tile
+// j: rows lo..hi of the trajectories i0 .. i0+n-1 (one 2D copy: n rows of the
+// trajectory dimension, each (hi - lo + 1) * d doubles).
+struct CopyOp {
+  int i0, n;
+  long long lo, hi;
+};
 struct HostCopyOut {
-  std::vector<std::vector<int>> by_tile;
-  const int* N = nullptr;
+  std::vector<std::vector<CopyOp>> ops;
   double *Yh = nullptr, *YPh = nullptr;  // host, leading dimension ldh
   long long ldh = 0;
   const double *Yd = nullptr, *YPd = nullptr;  // device, leading dimension ldd
   long long ldd = 0;
 };
+
+// The copy plan: after time tile j (rows up to e = (j+1) B are final), a
+// trajectory that ends in the tile copies its remaining rows up to N_i, and
+// the still-running trajectories copy their rows up to e when they form at
+// most kMaxRuns runs of consecutive indices (uniform N: one 2D copy per tile,
+// so almost all of the output crosses the host link while the solve runs;
+// scattered N: they wait for their own last tile).  Runs of consecutive
+// indices with equal row ranges share one 2D copy.
+constexpr int kMaxRuns = 32;
+std::vector<std::vector<CopyOp>> plan_copy_out(int M, const int* N, int B, int ntime) {
+  std::vector<std::vector<CopyOp>> ops(ntime);
+  std::vector<long long> copied(M, -1);  // last row already copied
+  auto emit = [&](int j, const std::vector<std::pair<int, long long>>& todo) {  // (trajectory, last row)
+    for (size_t k = 0; k < todo.size();) {
+      const int i0 = todo[k].first;
+      const long long lo = copied[i0] + 1, hi = todo[k].second;
+      size_t m = k + 1;
+      while (m < todo.size() && todo[m].first == todo[m - 1].first + 1 && todo[m].second == hi &&
+             copied[todo[m].first] + 1 == lo)
+        ++m;
+      ops[j].push_back({i0, (int)(m - k), lo, hi});
+      for (size_t q = k; q < m; ++q) copied[todo[q].first] = hi;
+      k = m;
+    }
+  };
+  for (int j = 0; j < ntime; ++j) {
+    const long long s = (long long)j * B, e = s + B;
+    std::vector<std::pair<int, long long>> ending, running;
+    int runs = 0;
+    for (int i = 0; i < M; ++i) {
+      if (N[i] <= s) continue;
+      if (N[i] <= e) {
+        ending.push_back({i, N[i]});
+      } else {
+        if (running.empty() || running.back().first != i - 1) ++runs;
+        running.push_back({i, e});
+      }
+    }
+    emit(j, ending);
+    if (runs <= kMaxRuns) emit(j, running);
+  }
+  return ops;
+}
 
 // The far / near launch sequence of one batched solve on stream st (tables
 // already on the device); with out, each time tile's finished trajectories
@@ -513,17 +560,19 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
       }
       CK(launch_batched_near(p->sys, A, n_active, s, B, wpc, split, st), "near kernel");
     }
-    if (out && j < (int)out->by_tile.size() && !out->by_tile[j].empty()) {
+    if (out && j < (int)out->ops.size() && !out->ops[j].empty()) {
       cudaEvent_t ev = p->hio_ev[j];
       CK(cudaEventRecord(ev, st), "event");
       CK(cudaStreamWaitEvent(p->copy_st, ev, 0), "event wait");
-      for (int i : out->by_tile[j]) {
-        const size_t bytes = (size_t)(out->N[i] + 1) * d * sizeof(double);
-        CK(cudaMemcpyAsync(out->Yh + (size_t)i * out->ldh * d, out->Yd + (size_t)i * out->ldd * d, bytes,
-                           cudaMemcpyDeviceToHost, p->copy_st), "copy-out");
+      const size_t hp = (size_t)out->ldh * d * sizeof(double), dp = (size_t)out->ldd * d * sizeof(double);
+      for (const CopyOp& c : out->ops[j]) {
+        const size_t width = (size_t)(c.hi - c.lo + 1) * d * sizeof(double);
+        const size_t ho = ((size_t)c.i0 * out->ldh + c.lo) * d, dof = ((size_t)c.i0 * out->ldd + c.lo) * d;
+        CK(cudaMemcpy2DAsync(out->Yh + ho, hp, out->Yd + dof, dp, width, c.n, cudaMemcpyDeviceToHost, p->copy_st),
+           "copy-out");
         if (out->YPh)
-          CK(cudaMemcpyAsync(out->YPh + (size_t)i * out->ldh * d, out->YPd + (size_t)i * out->ldd * d, bytes,
-                             cudaMemcpyDeviceToHost, p->copy_st), "copy-out");
+          CK(cudaMemcpy2DAsync(out->YPh + ho, hp, out->YPd + dof, dp, width, c.n, cudaMemcpyDeviceToHost,
+                               p->copy_st), "copy-out");
       }
     }
   }
@@ -1041,20 +1090,18 @@ abm_status abm_solve_batched_host(abm_plan p, int M, const double* alpha, const 
   Sched S;
   abm_status rs = schedule_batch(p, M, alpha, 1, 1.0, h, N, ldY, st, S, "abm_solve_batched_host");
   if (rs) return rs;
-  // inputs up, then the solve with each finished trajectory copied out behind
-  // the time tile that completes it
+  // inputs up, then the solve with finished rows copied out behind the time
+  // tiles that complete them
   CK(cudaMemcpyAsync(p->hio_params, params, (size_t)M * p->np * sizeof(double), cudaMemcpyHostToDevice, st),
      "params upload");
   CK(cudaMemcpyAsync(p->hio_y0, y0, (size_t)M * d * sizeof(double), cudaMemcpyHostToDevice, st), "y0 upload");
   HostCopyOut out;
-  out.by_tile.assign((S.nmax + B - 1) / B, {});
-  for (int i = 0; i < M; ++i) out.by_tile[(N[i] - 1) / B].push_back(i);
-  while (p->hio_ev.size() < out.by_tile.size()) {
+  out.ops = plan_copy_out(M, N, B, (S.nmax + B - 1) / B);
+  while (p->hio_ev.size() < out.ops.size()) {
     cudaEvent_t e;
     CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
     p->hio_ev.push_back(e);
   }
-  out.N = N;
   out.Yh = Y;
   out.YPh = YP;
   out.ldh = ldY;

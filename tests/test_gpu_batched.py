@@ -326,3 +326,24 @@ def test_batched_host_buffers_match_device_path(abm, prec):
             assert rel_err(got[i, : n + 1], Yd[i, : n + 1]) <= tol, (i, prec)
         assert rel_err(YPh.numpy()[i, 1: n + 1], YPd[i, 1: n + 1]) <= tol
         assert np.all(Yh.numpy()[i, n + 1:] == -7.0) and np.all(YPh.numpy()[i, n + 1:] == -7.0)
+
+
+def test_batched_host_progressive_copy_out(abm):
+    """Uniform and block-structured N: the still-running trajectories' rows
+    are copied out tile by tile as 2D copies; every row 0..N_i arrives, rows
+    beyond N_i stay untouched."""
+    for Ns in ([500] * 40, [300] * 20 + [640] * 20, [640] * 13 + [100] * 7 + [640] * 20):
+        M = len(Ns)
+        rng = np.random.default_rng(1611)
+        params = np.stack([np.full(M, 0.2), np.full(M, 0.2), rng.uniform(4, 12, M)], axis=1)
+        y0 = rng.uniform(-1, 1, (M, 3))
+        al, hh, NN = np.full(M, 0.9), np.full(M, 0.01), np.array(Ns)
+        plan = abm.Plan("rossler", n_max=int(NN.max()), max_batch=M)
+        Yd = plan.solve_batched(al, hh, NN, params, y0).cpu().numpy()
+        ldY = int(NN.max()) + 3
+        Yh = torch.full((M, ldY, 3), -7.0, dtype=torch.float64).pin_memory()
+        plan.solve_batched_host(al, hh, NN, params, y0, Y=Yh, ldY=ldY)
+        for i in range(M):
+            n = int(NN[i])
+            assert np.array_equal(Yh.numpy()[i, : n + 1], Yd[i, : n + 1]), (Ns[:3], i)
+            assert np.all(Yh.numpy()[i, n + 1:] == -7.0)
