@@ -46,7 +46,10 @@ typedef enum {
   ABM_ERR_OOM = 3,         /* device allocation failed                          */
   ABM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                */
   ABM_ERR_NONFINITE = 5,   /* a state or f value became NaN/Inf                 */
-  ABM_ERR_UNSUPPORTED = 6  /* valid request this build does not implement       */
+  ABM_ERR_UNSUPPORTED = 6, /* valid request this build does not implement       */
+  ABM_ERR_BOUNDS = 7       /* checked build only (libabm_gb300_checked.so, compiled
+                              with ABM_CHECKED): a kernel computed an index outside
+                              the buffer it addresses; the access was skipped    */
 } abm_status;
 
 /* Built-in right-hand sides f(t, y) with their dimension d and parameters:
@@ -133,7 +136,13 @@ typedef struct {
                           variant of the predictor-corrector).  Forward solves
                           only: abm_adjoint returns ABM_ERR_UNSUPPORTED for m > 1;
                           YP still receives the predictor                      */
-  int reserved[6];     /* must be zero                                            */
+  int test_bad_index;  /* testing only, 0 = off; accepted by the checked build
+                          alone (ABM_ERR_UNSUPPORTED otherwise).  k > 0: the
+                          batched near kernel offsets the output row of
+                          trajectory k-1 past the end of Y, so the checked
+                          kernel skips that store and the call reports
+                          ABM_ERR_BOUNDS                                        */
+  int reserved[5];     /* must be zero                                            */
 } abm_plan_opts;
 
 /* Fills *o with the defaults (FP64, n_max = 0, tile_B = 0 ...). */
@@ -165,7 +174,9 @@ abm_status abm_plan_destroy(abm_plan p);
  * time tile `unit`, 2 = a single-trajectory far CTA waiting for the rows
  * before time tile `unit`, 3..5 = the tensor-core far kernel of column tile
  * `unit` (3 loader, 4 MMA issuer waiting for an accumulator, 5 MMA issuer
- * waiting for the operands of K block `position`). */
+ * waiting for the operands of K block `position`); for ABM_ERR_BOUNDS (the
+ * checked build) kernel << 52 | index of the first index found outside its
+ * buffer. */
 abm_status abm_plan_sync(abm_plan p, void* stream, int64_t* where);
 
 /* Message of the last failure on this plan (owned by the plan, valid until

@@ -14,12 +14,15 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libabm_gb300.so")
+# the same library compiled with ABM_CHECKED: every layout-derived index is
+# checked against its buffer (ABM_ERR_BOUNDS instead of an access outside it)
+CHECKED_LIB_PATH = os.path.join(_HERE, "libabm_gb300_checked.so")
 
 SYSTEMS = {"linear": 0, "manufactured": 1, "lorenz": 2, "chen": 3, "rossler": 4, "financial": 5,
            "hindmarsh_rose": 6}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
 STATUS = {0: "ABM_OK", 1: "ABM_ERR_INVALID_ARG", 2: "ABM_ERR_CUDA", 3: "ABM_ERR_OOM",
-          4: "ABM_ERR_TIMEOUT", 5: "ABM_ERR_NONFINITE", 6: "ABM_ERR_UNSUPPORTED"}
+          4: "ABM_ERR_TIMEOUT", 5: "ABM_ERR_NONFINITE", 6: "ABM_ERR_UNSUPPORTED", 7: "ABM_ERR_BOUNDS"}
 
 # Every symbol include/abm.h declares (checked by the CPU test suite).
 EXPORTS = ["abm_plan_opts_default", "abm_system_dim", "abm_system_nparams", "abm_plan_create",
@@ -42,23 +45,23 @@ class PlanOpts(ctypes.Structure):
                 ("spin_timeout_cycles", ctypes.c_longlong), ("test_withhold_tile", ctypes.c_int),
                 ("profile", ctypes.c_int), ("near_warps", ctypes.c_int), ("far_split", ctypes.c_int),
                 ("near_split", ctypes.c_int), ("corrector_passes", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("test_bad_index", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
-_lib = None
+_libs = {}
 _lock = threading.Lock()
 _vp, _dp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
 
 
 def load(path: str = LIB_PATH):
     """Loads the library (builds it first when sources are newer).  Raises if
-    it cannot be built or loaded; there is no fallback."""
-    global _lib
+    it cannot be built or loaded; there is no fallback.  path: LIB_PATH, or
+    CHECKED_LIB_PATH for the bounds-checked build."""
     with _lock:
-        if _lib is not None:
-            return _lib
+        if path in _libs:
+            return _libs[path]
         from . import build as _build
-        if not _build.up_to_date():
+        if not _build.up_to_date(path):
             _build.build()
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library {path} is missing")
@@ -90,7 +93,7 @@ def load(path: str = LIB_PATH):
         for name in EXPORTS:
             if name not in ("abm_plan_opts_default", "abm_last_error", "abm_system_dim", "abm_system_nparams"):
                 getattr(lib, name).restype = I
-        _lib = lib
+        _libs[path] = lib
         return lib
 
 
@@ -146,8 +149,9 @@ class Plan:
     def __init__(self, system: str, n_max: int, max_batch: int = 0, prec: str = "fp64", tile_B: int = 0,
                  far_ctas: int = 0, use_graph: bool = False, spin_timeout_cycles: int = 0,
                  test_withhold_tile: int = 0, profile: bool = False, near_warps: int = 0,
-                 far_split: int = 0, near_split: int = 0, corrector_passes: int = 1):
-        self.lib = load()
+                 far_split: int = 0, near_split: int = 0, corrector_passes: int = 1, checked: bool = False,
+                 test_bad_index: int = 0):
+        self.lib = load(CHECKED_LIB_PATH if checked else LIB_PATH)
         self.system = system
         self.d = self.lib.abm_system_dim(SYSTEMS[system])
         self.np = self.lib.abm_system_nparams(SYSTEMS[system])
@@ -167,6 +171,7 @@ class Plan:
         o.far_split = int(far_split)
         o.near_split = int(near_split)
         o.corrector_passes = int(corrector_passes)
+        o.test_bad_index = int(test_bad_index)
         h = _vp()
         st = self.lib.abm_plan_create(ctypes.byref(h), SYSTEMS[system], ctypes.byref(o))
         if st != 0:

@@ -485,8 +485,11 @@ cudaError_t launch_adjoint_setup(int sys, const AdjArgs& A, int n_tiles, cudaStr
   return cudaGetLastError();
 }
 
+// static: internal linkage, so the flag below belongs to this build of the
+// library (a function-local static of an external template is one object for
+// the whole process, shared by every loaded build)
 template <int SYS, int HS>
-cudaError_t launch_adjoint_near_t(const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+static cudaError_t launch_adjoint_near_t(const AdjArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
   constexpr int D = Sys<SYS>::D;
   const size_t smem = (size_t)(130 + 4 * HS) * kTrajPerTile * D * sizeof(double);
   static bool attr_set = false;  // per instantiation

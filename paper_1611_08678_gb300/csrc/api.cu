@@ -37,9 +37,9 @@ cudaError_t launch_fill_fsh(const double* F, long long s, __nv_bfloat16* Fsh, lo
 cudaError_t launch_sum_partials(const double* far, int ksplit, int n_tiles, double* P, double* C, cudaStream_t st);
 cudaError_t launch_adjoint_setup(int sys, const AdjArgs& A, int n_tiles, cudaStream_t st);
 cudaError_t launch_import_history(int d, const BatchArgs& A, int n_tiles, long long s0, const double* Fin,
-                                  long long ldF, cudaStream_t st);
+                                  long long ldF, long long fin_elems, cudaStream_t st);
 cudaError_t launch_export_history(int d, const BatchArgs& A, int n_tiles, long long rows, double* Fout, long long ldF,
-                                  cudaStream_t st);
+                                  long long fout_elems, cudaStream_t st);
 cudaError_t launch_adjoint_near(int sys, const AdjArgs& A, int n_active, long long s, int nb, int wpc,
                                 int split, cudaStream_t st);
 cudaError_t launch_adjoint_finish(int sys, const AdjArgs& A, int M, cudaStream_t st);
@@ -275,6 +275,10 @@ FarTcArgs far_tc_args(abm_plan p, const TileDesc* tiles, const CUtensorMap* tmap
   T.n_tiles = n_tiles;
   T.ksplit = ks;
   T.f_kblocks = (int)(p->fsh_ld / 64);
+  const long long gcols = (long long)p->max_tiles * kTrajPerTile * p->d;
+  T.f_map_rows = gcols * (p->fsh_ld / 64) * (tmapF == p->d_tmapX ? 2 : 1);  // adjoint planes: 2 tiles per tile
+  T.w_map_rows = 2 * p->Lx;
+  T.far_elems = (long long)p->farb_cap;
   return T;
 }
 
@@ -324,6 +328,7 @@ struct Sched {
   int n_tiles = 0, nmax = 0, ksplit = 1;
   bool per_comp = false;                          // some group's orders differ per component
   size_t hist_elems = 0;
+  int M = 0;
 };
 
 // alpha: M orders (astride = 1, every component) or M x d (astride = d), each
@@ -355,6 +360,7 @@ abm_status schedule_batch(abm_plan p, int M, const double* alpha, int astride, d
     for (int c = 0; c < d; ++c)
       if (std::find(values.begin(), values.end(), t[c]) == values.end()) values.push_back(t[c]);
   }
+  S.M = M;
   const int n_groups = (int)S.groups.size();
   if (n_groups > kMaxWeightSets || (int)values.size() > kMaxWeightSets)
     return fail(p, ABM_ERR_UNSUPPORTED, std::string(who) + ": more than " + std::to_string(kMaxWeightSets) +
@@ -616,6 +622,12 @@ BatchArgs batch_args(abm_plan p, const Sched& S, const double* params, const dou
   A.ldY = ldY;
   A.status = p->status;
   A.passes = p->o.corrector_passes > 1 ? p->o.corrector_passes : 1;
+  A.f_elems = (long long)p->fb_cap;
+  A.w_elems = (long long)p->Mw + 1;
+  A.far_elems = (long long)p->farb_cap;
+  A.y_elems = (long long)S.M * ldY * d;
+  A.fsh_plane_elems = A.fsh_plane;
+  A.bad_traj = p->o.test_bad_index > 0 ? p->o.test_bad_index - 1 : -1;
   return A;
 }
 
@@ -656,6 +668,10 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
   if (o->near_split != 0 && o->near_split != 1 && o->near_split != 2 && o->near_split != 4 && o->near_split != 8)
     return ABM_ERR_INVALID_ARG;
   if (o->corrector_passes < 0 || o->corrector_passes > 8) return ABM_ERR_INVALID_ARG;
+  if (o->test_bad_index < 0) return ABM_ERR_INVALID_ARG;
+#ifndef ABM_CHECKED
+  if (o->test_bad_index != 0) return ABM_ERR_UNSUPPORTED;  // only a checked build may offset an index
+#endif
   const bool tc_prec = o->prec == ABM_PREC_BF16X3_FAR || o->prec == ABM_PREC_BF16X6_FAR;
   if (tc_prec && (sys_dim(sys) != 3 || (o->tile_B && o->tile_B != 64))) return ABM_ERR_UNSUPPORTED;
   abm_plan p = new abm_plan_s();
@@ -892,6 +908,9 @@ abm_status solve_single(abm_plan p, const char* who, const double* alpha, double
   A.withhold_tile = p->o.test_withhold_tile > 0 ? p->o.test_withhold_tile - 1 : -1;
   A.passes = p->o.corrector_passes > 1 ? p->o.corrector_passes : 1;
   A.start_tile = n0 / kPersistB;
+  A.f_elems = (long long)(((p->o.n_max + p->B - 1) / p->B) * p->B + 1 + p->B) * p->d;
+  A.w_elems = (long long)p->Mw + 1;
+  A.partial_elems = (long long)kPersistRing * (p->Gp - 1) * kPersistB * 2 * p->d;
   if (A.start_tile > 0)
     CK(cudaMemcpyAsync(p->F1, F_in, (size_t)(A.start_tile * kPersistB + 1) * p->d * sizeof(double),
                        cudaMemcpyDefault, st), "history import");
@@ -1043,7 +1062,8 @@ abm_status abm_history_batched(abm_plan p, int M, const double* alpha, const dou
   abm_status rs = schedule_batch(p, M, alpha, p->d, 2.0, h, N, (long long)nmax + 1, st, S, "abm_history_batched");
   if (rs) return rs;
   const BatchArgs A = batch_args(p, S, nullptr, nullptr, nullptr, nullptr, nullptr, S.nmax + 1);
-  CK(launch_export_history(p->d, A, S.n_tiles, std::min<long long>(rows, (long long)S.nmax + 1), F, ldF, st),
+  CK(launch_export_history(p->d, A, S.n_tiles, std::min<long long>(rows, (long long)S.nmax + 1), F, ldF,
+                           (long long)M * ldF * p->d, st),
      "history export kernel");
   return ABM_OK;
 }
@@ -1063,9 +1083,11 @@ abm_status abm_solve_batched_resume(abm_plan p, int M, const double* alpha, cons
   abm_status rs = schedule_batch(p, M, alpha, p->d, 2.0, h, N, ldY, st, S, "abm_solve_batched_resume");
   if (rs) return rs;
   BatchArgs A = batch_args(p, S, params, y0, y0d, Y, YP, ldY);
+  A.y_elems = (long long)M * ldY * p->d;
   A.resume_row = (long long)(n0 / p->B) * p->B;
   if (A.resume_row > 0)
-    CK(launch_import_history(p->d, A, S.n_tiles, A.resume_row, F, ldF, st), "history import kernel");
+    CK(launch_import_history(p->d, A, S.n_tiles, A.resume_row, F, ldF, (long long)M * ldF * p->d, st),
+       "history import kernel");
   return enqueue_batched(p, S, A, st);
 }
 
@@ -1247,6 +1269,10 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
   F.F = p->Xadj;
   F.far = p->farb;
   F.status = p->status;
+  F.f_elems = 2 * (long long)p->fb_cap;
+  F.w_elems = (long long)p->Mw + 1;
+  F.far_elems = (long long)p->farb_cap;
+  F.bad_traj = -1;
   const int ntime = (S.nmax + B - 1) / B;
   int n_active = n_tiles;
   for (int j = 0; j < ntime; ++j) {

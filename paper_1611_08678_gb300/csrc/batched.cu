@@ -46,6 +46,7 @@ __global__ void batched_setup_kernel(BatchArgs A) {
   if (A.resume_row > 0) return;  // f_0 was imported with the history; Y row 0 is the caller's
   S::f(p, alpha, 0.0, y0, f0);
   double* F = A.F + T.f_off;
+  if (!in_bounds(A.status, kChkSetup, T.f_off + lane * D + D - 1, A.f_elems)) return;
 #pragma unroll
   for (int c = 0; c < D; ++c) F[lane * D + c] = f0[c];
   if (A.F32) {
@@ -53,7 +54,7 @@ __global__ void batched_setup_kernel(BatchArgs A) {
 #pragma unroll
     for (int c = 0; c < D; ++c) F32[lane * D + c] = (float)f0[c];
   }
-  if (traj >= 0) {
+  if (traj >= 0 && in_bounds(A.status, kChkSetup, (long long)traj * A.ldY * D + D - 1, A.y_elems)) {
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       A.Y[(size_t)traj * A.ldY * D + c] = y0[c];
@@ -111,15 +112,18 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
     wsb_[m / 65][m % 65] = A.bucket_b[bk + m / 65][m % 65];
     wsa_[m / 65][m % 65] = A.bucket_a[bk + m / 65][m % 65];
   }
+  const bool w_ok = in_bounds(A.status, kChkNear, s + 63, A.w_elems);
   for (int m = threadIdx.x; m < D * 64; m += NT) {
-    bns_[m / 64][m % 64] = A.bucket_b[bk + m / 64][s + m % 64];
-    cns_[m / 64][m % 64] = A.bucket_c[bk + m / 64][s + m % 64];
+    bns_[m / 64][m % 64] = w_ok ? A.bucket_b[bk + m / 64][s + m % 64] : 0.0;
+    cns_[m / 64][m % 64] = w_ok ? A.bucket_c[bk + m / 64][s + m % 64] : 0.0;
   }
   const double* wsb = wsb_[c];  // this warp's component
   const double* wsa = wsa_[c];
   const double* bns = bns_[c];
   const double* cns = cns_[c];
-  for (int m = threadIdx.x; m < ld; m += NT) Fw[0][m] = F[s * ld + m];
+  // the tile's rows s .. s + nb are read or written below
+  const bool f_ok = in_bounds(A.status, kChkNear, T.f_off + (s + nb + 1) * ld - 1, A.f_elems);
+  for (int m = threadIdx.x; m < ld; m += NT) Fw[0][m] = f_ok ? F[s * ld + m] : 0.0;
   for (int m = threadIdx.x; m < HS * ld; m += NT) {  // step 0 has no earlier window rows (helpers)
     Rp[0][m / ld][m % ld] = 0.0;
     Rc[0][m / ld][m % ld] = 0.0;
@@ -143,9 +147,13 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
     const double* __restrict__ farP = A.far + (((size_t)tile * 2) * A.B) * ld + col;
     const size_t far_q_stride = (size_t)A.n_tiles * 2 * A.B * ld;
     const size_t far_c_off = (size_t)A.B * ld;
+    const bool far_ok = s <= 1 || in_bounds(A.status, kChkNear,
+                                            (long long)((A.ksplit - 1) * far_q_stride + far_c_off +
+                                                        (size_t)(((size_t)tile * 2) * A.B) * ld + (A.B - 1) * ld + col),
+                                            A.far_elems);
     // far partial sums of the next target, loaded a step ahead
     double nxp = 0.0, nxc = 0.0;
-    if (s > 1) {
+    if (s > 1 && far_ok) {
       nxp = sum_parts(farP, A.ksplit, far_q_stride);
       nxc = sum_parts(farP + far_c_off, A.ksplit, far_q_stride);
     }
@@ -156,7 +164,7 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
       const int par = i & 1;
       double sp = fma(bns[i], F0c, nxp), sc = fma(cns[i], F0c, nxc);
       nxp = nxc = 0.0;
-      if (s > 1 && i + 1 < nb) {
+      if (s > 1 && i + 1 < nb && far_ok) {
         nxp = sum_parts(farP + (size_t)(i + 1) * ld, A.ksplit, far_q_stride);
         nxc = sum_parts(farP + far_c_off + (size_t)(i + 1) * ld, A.ksplit, far_q_stride);
       }
@@ -215,11 +223,16 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
       }
       const double fy = S::fc(c, p, alpha, t1, yv);
       Fw[i + 1][col] = fy;
-      F[(n + 1) * ld + col] = fy;
-      if (F32) F32[(n + 1) * ld + col] = (float)fy;
-      if (n + 1 <= Ntraj) {
-        A.Y[((size_t)traj * A.ldY + (n + 1)) * D + c] = y;
-        if (A.YP) A.YP[((size_t)traj * A.ldY + (n + 1)) * D + c] = yp;
+      if (f_ok) {
+        F[(n + 1) * ld + col] = fy;
+        if (F32) F32[(n + 1) * ld + col] = (float)fy;
+      }
+      // the output row; a testing option of the checked build moves one
+      // trajectory's row past the end of Y
+      const long long yrow = (n + 1) + ((kChecked && traj == A.bad_traj) ? A.ldY * (long long)(1 << 20) : 0);
+      if (n + 1 <= Ntraj && in_bounds(A.status, kChkNear, ((long long)traj * A.ldY + yrow) * D + c, A.y_elems)) {
+        A.Y[((size_t)traj * A.ldY + yrow) * D + c] = y;
+        if (A.YP) A.YP[((size_t)traj * A.ldY + yrow) * D + c] = yp;
         if (!reported && !(finite_bits(y) && finite_bits(fy))) {
           report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
           reported = true;
@@ -275,6 +288,7 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
         v[2][r] = pcs[2];
       }
       const size_t off = (((size_t)T.slot * (A.fsh_ld / 64) + s / 64) * ld + cc) * 64 + part * 8;
+      if (!in_bounds(A.status, kChkNear, (long long)off + 7, A.fsh_plane_elems)) continue;
 #pragma unroll
       for (int pc = 0; pc < 3; ++pc)
         *reinterpret_cast<uint4*>(A.Fsh + (size_t)pc * A.fsh_plane + off) = *reinterpret_cast<const uint4*>(v[pc]);
@@ -320,15 +334,17 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
     wsb_[m / 65][m % 65] = A.bucket_b[bk + m / 65][m % 65];
     wsa_[m / 65][m % 65] = A.bucket_a[bk + m / 65][m % 65];
   }
+  const bool w_ok = in_bounds(A.status, kChkNearSplit, s + 63, A.w_elems);
   for (int m = threadIdx.x; m < D * 64; m += NT) {
-    bns_[m / 64][m % 64] = A.bucket_b[bk + m / 64][s + m % 64];
-    cns_[m / 64][m % 64] = A.bucket_c[bk + m / 64][s + m % 64];
+    bns_[m / 64][m % 64] = w_ok ? A.bucket_b[bk + m / 64][s + m % 64] : 0.0;
+    cns_[m / 64][m % 64] = w_ok ? A.bucket_c[bk + m / 64][s + m % 64] : 0.0;
   }
   const double* wsb = wsb_[c];  // this warp's component
   const double* wsa = wsa_[c];
   const double* bns = bns_[c];
   const double* cns = cns_[c];
-  for (int m = threadIdx.x; m < ldc; m += NT) Fw[0][m] = F[s * ldt + part * ldc + m];
+  const bool f_ok = in_bounds(A.status, kChkNearSplit, Td.f_off + (s + nb + 1) * ldt - 1, A.f_elems);
+  for (int m = threadIdx.x; m < ldc; m += NT) Fw[0][m] = f_ok ? F[s * ldt + part * ldc + m] : 0.0;
   const int kfirst = s > 1 ? 0 : 1;  // window rows relative to s (row 0 is f_0 when s = 0)
   const double g = A.bucket_g[bk + c];
   const long long Ntraj = traj >= 0 ? (long long)A.N[traj] : 0;
@@ -346,8 +362,12 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
   const double* __restrict__ farP = A.far + (((size_t)tile * 2) * A.B) * ldt + col;
   const size_t far_q_stride = (size_t)A.n_tiles * 2 * A.B * ldt;
   const size_t far_c_off = (size_t)A.B * ldt;
+  const bool far_ok = s <= 1 || in_bounds(A.status, kChkNearSplit,
+                                          (long long)((A.ksplit - 1) * far_q_stride + far_c_off +
+                                                      (size_t)(((size_t)tile * 2) * A.B) * ldt + (A.B - 1) * ldt + col),
+                                          A.far_elems);
   double nxp = 0.0, nxc = 0.0;  // far sums of the next target, loaded a step ahead
-  if (s > 1 && l == 0) {
+  if (s > 1 && l == 0 && far_ok) {
     nxp = sum_parts(farP, A.ksplit, far_q_stride);
     nxc = sum_parts(farP + far_c_off, A.ksplit, far_q_stride);
   }
@@ -384,7 +404,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
     sp = fma(bns[i], F0c, sp);
     sc = fma(cns[i], F0c, sc);
     nxp = nxc = 0.0;
-    if (s > 1 && i + 1 < nb && l == 0) {
+    if (s > 1 && i + 1 < nb && l == 0 && far_ok) {
       nxp = sum_parts(farP + (size_t)(i + 1) * ldt, A.ksplit, far_q_stride);
       nxc = sum_parts(farP + far_c_off + (size_t)(i + 1) * ldt, A.ksplit, far_q_stride);
     }
@@ -417,11 +437,14 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
     const double fy = S::fc(c, p, alpha, t1, yv);
     if (l == 0) {
       Fw[i + 1][cloc] = fy;
-      F[(n + 1) * ldt + col] = fy;
-      if (F32) F32[(n + 1) * ldt + col] = (float)fy;
-      if (n + 1 <= Ntraj) {
-        A.Y[((size_t)traj * A.ldY + (n + 1)) * D + c] = y;
-        if (A.YP) A.YP[((size_t)traj * A.ldY + (n + 1)) * D + c] = yp;
+      if (f_ok) {
+        F[(n + 1) * ldt + col] = fy;
+        if (F32) F32[(n + 1) * ldt + col] = (float)fy;
+      }
+      const long long yrow = (n + 1) + ((kChecked && traj == A.bad_traj) ? A.ldY * (long long)(1 << 20) : 0);
+      if (n + 1 <= Ntraj && in_bounds(A.status, kChkNearSplit, ((long long)traj * A.ldY + yrow) * D + c, A.y_elems)) {
+        A.Y[((size_t)traj * A.ldY + yrow) * D + c] = y;
+        if (A.YP) A.YP[((size_t)traj * A.ldY + yrow) * D + c] = yp;
         if (!reported && !(finite_bits(y) && finite_bits(fy))) {
           report_status(A.status, ABM_ERR_NONFINITE, traj, n + 1);
           reported = true;
@@ -448,6 +471,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
         v[2][rr] = pcs[2];
       }
       const size_t off = (((size_t)Td.slot * (A.fsh_ld / 64) + s / 64) * ldt + part * ldc + cc) * 64 + prt * 8;
+      if (!in_bounds(A.status, kChkNearSplit, (long long)off + 7, A.fsh_plane_elems)) continue;
 #pragma unroll
       for (int pc = 0; pc < 3; ++pc)
         *reinterpret_cast<uint4*>(A.Fsh + (size_t)pc * A.fsh_plane + off) = *reinterpret_cast<const uint4*>(v[pc]);
@@ -480,7 +504,15 @@ __global__ void __launch_bounds__(256) batched_far_fp64_kernel(BatchArgs A, long
   for (int r = 0; r < R; ++r)
 #pragma unroll
     for (int c = 0; c < D; ++c) accP[r][c] = accC[r][c] = 0.0;
-  if (kb < ke) {
+  // rows [kb, ke) of the tile and lags up to s + B - 1 - kb are read; the
+  // partial sums of this split are written below
+  const bool ok = kb >= ke || (in_bounds(A.status, kChkFarFp64, T.f_off + ke * ld - 1, A.f_elems) &&
+                               in_bounds(A.status, kChkFarFp64, s + B - 1 - kb, A.w_elems));
+  const bool out_ok =
+      in_bounds(A.status, kChkFarFp64, ((((long long)q * A.n_tiles + tile) * 2 + 1) * B + B - 1) * ld + ld - 1,
+                A.far_elems);
+  if (!out_ok) return;
+  if (kb < ke && ok) {
     double wbv[R], wav[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { wbv[r] = wb[s + i0 + r - kb]; wav[r] = wa[s + i0 + r - kb]; }
@@ -532,7 +564,12 @@ __global__ void __launch_bounds__(512) batched_far_fp32_kernel(BatchArgs A, long
   for (int r = 0; r < R; ++r)
 #pragma unroll
     for (int c = 0; c < D; ++c) dP[r][c] = dC[r][c] = 0.0;
-  for (long long k0 = kb; k0 < ke; k0 += KB) {
+  const bool ok = kb >= ke || (in_bounds(A.status, kChkFarFp32, T.f_off + ke * ld - 1, A.f_elems) &&
+                               in_bounds(A.status, kChkFarFp32, s + B - 1 - kb, A.w_elems));
+  if (!in_bounds(A.status, kChkFarFp32, ((((long long)q * A.n_tiles + tile) * 2 + 1) * B + B - 1) * ld + ld - 1,
+                 A.far_elems))
+    return;
+  for (long long k0 = kb; ok && k0 < ke; k0 += KB) {
     const long long k1 = min(ke, k0 + KB);
     float accP[R][D], accC[R][D];
 #pragma unroll
@@ -589,6 +626,11 @@ __global__ void __launch_bounds__(256) batched_far_percomp_kernel(BatchArgs A, l
   const long long kb = A.far_k0 + (long long)q * chunk, ke = min(s, kb + chunk);
   const long long blk = KB == 0 ? (ke > kb ? ke - kb : 1) : KB;
   const int i0 = warp * R;
+  const bool ok = kb >= ke || (in_bounds(A.status, kChkFarPerComp, T.f_off + ke * ld - 1, A.f_elems) &&
+                               in_bounds(A.status, kChkFarPerComp, s + B - 1 - kb, A.w_elems));
+  if (!ok || !in_bounds(A.status, kChkFarPerComp, ((((long long)q * A.n_tiles + tile) * 2 + 1) * B + B - 1) * ld + ld - 1,
+                        A.far_elems))
+    return;
   for (int c = 0; c < D; ++c) {
     const real* __restrict__ wb;
     const real* __restrict__ wa;
@@ -642,8 +684,11 @@ cudaError_t launch_batched_setup(int sys, const BatchArgs& A, int n_tiles, cudaS
   return cudaGetLastError();
 }
 
+// static: internal linkage, so the flag below belongs to this build of the
+// library (a function-local static of an external template is one object for
+// the whole process, shared by every loaded build)
 template <int SYS, int HS>
-cudaError_t launch_near_t(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+static cudaError_t launch_near_t(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
   constexpr int D = Sys<SYS>::D;
   const size_t smem = (size_t)(65 + 4 * HS) * kTrajPerTile * D * sizeof(double);
   static bool attr_set = false;  // per instantiation; a plan is used from one thread

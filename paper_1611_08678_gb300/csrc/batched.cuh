@@ -61,6 +61,9 @@ struct BatchArgs {
   int passes;              // corrector passes per step (1 = PECE)
   long long resume_row;    // resume: history rows 0..resume_row were imported and Y rows up
                            // to it are the caller's (0 = a fresh solve)
+  // extents of the buffers above, in elements (checked build)
+  long long f_elems, w_elems, far_elems, y_elems, fsh_plane_elems;
+  int bad_traj;            // testing (checked build): trajectory whose output row is offset, -1 = off
 };
 
 // Arguments of the tensor-core far kernel (far_tc.cu).
@@ -77,6 +80,9 @@ struct FarTcArgs {
   int n_tiles;
   int ksplit;
   int f_kblocks;             // 64-row K blocks per column tile in the history pieces
+  // extents (checked build): rows of the history and Toeplitz tensor maps,
+  // elements of far
+  long long f_map_rows, w_map_rows, far_elems;
 };
 
 // Arguments of the adjoint kernels (adjoint.cu).

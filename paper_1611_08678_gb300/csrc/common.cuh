@@ -39,6 +39,36 @@ __device__ __forceinline__ void report_timeout(unsigned long long* status, int s
   atomicCAS(status, 0ull, w);
 }
 
+// ---- checked build (compiled with ABM_CHECKED) ----
+// Every index a kernel derives from the host's layout (tile offsets, leading
+// dimensions, lags, tensor-map coordinates, partial-sum slots) is compared
+// with the extent of the buffer it addresses; an index outside is not
+// accessed, and the first one is reported as ABM_ERR_BOUNDS with the site in
+// bits 52..59 and the index in bits 0..51 of the status word.  Without
+// ABM_CHECKED in_bounds() is the constant true and costs nothing.
+#ifdef ABM_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+enum CheckSite : int {
+  kChkSetup = 1, kChkNear = 2, kChkNearSplit = 3, kChkFarFp64 = 4, kChkFarFp32 = 5, kChkFarPerComp = 6,
+  kChkFarTc = 7, kChkSingle = 8, kChkImport = 9, kChkExport = 10, kChkAdjoint = 11, kChkWeights = 12
+};
+
+__device__ __forceinline__ bool in_bounds(unsigned long long* status, int site, long long idx, long long extent) {
+  if constexpr (!kChecked) {
+    return true;
+  } else {
+    if (idx >= 0 && idx < extent) return true;
+    unsigned long long w = ((unsigned long long)ABM_ERR_BOUNDS << 60) | ((unsigned long long)(site & 0xFF) << 52) |
+                           ((unsigned long long)idx & 0xFFFFFFFFFFFFFull);
+    atomicCAS(status, 0ull, w);
+    return false;
+  }
+}
+
 // x is neither infinite nor NaN: an exponent-bit test on the integer pipe
 // (GB300's FP64 pipe is the bottleneck of the sequential steps).
 __device__ __forceinline__ bool finite_bits(double x) {

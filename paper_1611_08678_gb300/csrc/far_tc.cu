@@ -125,7 +125,21 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
   const int nkb_total = (int)(A.s / KB);
   const int per_q = (nkb_total + A.ksplit - 1) / A.ksplit;
   const int kb_begin = q * per_q;
-  const int nkb = max(0, min(nkb_total, kb_begin + per_q) - kb_begin);
+  int nkb = max(0, min(nkb_total, kb_begin + per_q) - kb_begin);
+  if constexpr (kChecked) {
+    // every box this CTA loads lies inside its tensor map and every sum it
+    // stores inside far; otherwise it loads and stores nothing
+    const long long kl = kb_begin + (nkb > 0 ? nkb : 1) - 1;
+    const long long yf_last = ((long long)A.tiles[tile].slot * A.f_kblocks + kl) * NCOL + NCOL - 1;
+    const long long yw_first = (long long)((A.Lbase - A.s) / KB + kb_begin) * 128;
+    const long long yw_last = (long long)((A.Lbase - A.s) / KB + kl) * 128 + 127;
+    const long long out_last = (((long long)tile * 2 + 1) * 64 + 63) * NCOL + NCOL - 1;
+    if (nkb > 0 && !(in_bounds(A.status, kChkFarTc, yf_last, A.f_map_rows) &&
+                     in_bounds(A.status, kChkFarTc, yw_first, A.w_map_rows) &&
+                     in_bounds(A.status, kChkFarTc, yw_last, A.w_map_rows) &&
+                     in_bounds(A.status, kChkFarTc, out_last, A.far_elems)))
+      nkb = 0;
+  }
   const int nchunks = (nkb + CB - 1) / CB;
   const int xb0 = (int)((A.Lbase - A.s) / KB);  // Toeplitz block of history block 0
 
@@ -376,8 +390,11 @@ cudaError_t launch_build_wx(const double* b, const double* a, long long Mw, long
   return cudaGetLastError();
 }
 
+// static: internal linkage, so the flag below belongs to this build of the
+// library (a function-local static of an external template is one object for
+// the whole process, shared by every loaded build)
 template <int KIND>
-cudaError_t launch_far_tc_t(const FarTcArgs& A, int n_active, cudaStream_t st) {
+static cudaError_t launch_far_tc_t(const FarTcArgs& A, int n_active, cudaStream_t st) {
   const size_t smem = far_tc_smem_bytes_t<KIND>();
   static bool attr = false;  // set once per instantiation
   if (!attr) {

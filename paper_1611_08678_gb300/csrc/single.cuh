@@ -43,6 +43,7 @@ struct PersistArgs {
   int passes;                  // corrector passes per step (1 = PECE)
   int start_tile;              // resume: first time tile stepped; F rows 0..start_tile*B hold
                                // the history of an earlier solve (0 = a fresh solve)
+  long long f_elems, w_elems, partial_elems;  // extents of F, each weight vector, partial (checked build)
 };
 
 cudaError_t launch_far_single(int d, const FarSingleArgs& A, int B, int grid, cudaStream_t st);

@@ -166,9 +166,13 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
       __syncthreads();
       if (!ok_s) return;
       const long long K = e - 1, chunk = (K + W - 1) / W;
-      const long long c0 = 1 + (long long)w * chunk, c1 = min(e, c0 + chunk);
-      far_chunk<D, PB, 4, PT, NC>(A.F, A.b, A.a, s, c0, c1, dyn,
-                              A.partial + ((size_t)(j % PR) * W + w) * (PB * V));
+      long long c0 = 1 + (long long)w * chunk, c1 = min(e, c0 + chunk);
+      const size_t pofs = ((size_t)(j % PR) * W + w) * (PB * V);
+      if (!in_bounds(A.status, kChkSingle, (long long)pofs + PB * V - 1, A.partial_elems)) return;
+      if (c0 < c1 && !(in_bounds(A.status, kChkSingle, c1 * D - 1, A.f_elems) &&
+                       in_bounds(A.status, kChkSingle, s + PB - 1 - c0, A.w_elems)))
+        c1 = c0;  // reads nothing: zero sums
+      far_chunk<D, PB, 4, PT, NC>(A.F, A.b, A.a, s, c0, c1, dyn, A.partial + pofs);
       __threadfence();
       __syncthreads();
       if (tid == 0 && j != A.withhold_tile) atomicAdd(far_count + (j % PR), 1ull);
@@ -246,6 +250,13 @@ __global__ void __launch_bounds__(PT, 1) single_persistent_kernel(PersistArgs A)
   for (int j = j0; j < ntiles; ++j) {
     const long long s = (long long)j * PB;
     const int nb = (int)min((long long)PB, (long long)N - s);
+    if (kChecked && tid == 0)  // rows written and lags read in this tile
+      ok_s = in_bounds(A.status, kChkSingle, (s + nb + 1) * D - 1, A.f_elems) &&
+             in_bounds(A.status, kChkSingle, s + PB - 1, A.w_elems);
+    if (kChecked) {
+      __syncthreads();
+      if (!ok_s) return;
+    }
     // ---- far sums of this tile: fixed-order sum of the W partials ----
     if (j >= 2) {
       if (tid == 0) {

@@ -120,3 +120,25 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
     if not torch.cuda.is_available():
         with pytest.raises(RuntimeError):
             abm.Plan("lorenz", n_max=10)
+
+
+def test_checked_library_exports_the_same_symbols():
+    """libabm_gb300_checked.so is the same sources compiled with ABM_CHECKED."""
+    lib = abm.load(abm.CHECKED_LIB_PATH)
+    declared = _declared_functions()
+    assert not [n for n in sorted(declared) if not hasattr(lib, n)]
+
+
+def test_only_the_checked_build_accepts_an_offset_index():
+    """The testing option that moves one output row past the end of Y is
+    refused by the plain library before any CUDA call: without the checks it
+    would write outside the buffer."""
+    lib = abm.load()
+    h = ctypes.c_void_p()
+    o = abm.PlanOpts()
+    lib.abm_plan_opts_default(ctypes.byref(o))
+    o.n_max, o.max_batch, o.test_bad_index = 100, 4, 1
+    assert lib.abm_plan_create(ctypes.byref(h), 2, ctypes.byref(o)) == 6
+    assert not h.value
+    o.test_bad_index = -1
+    assert lib.abm_plan_create(ctypes.byref(h), 2, ctypes.byref(o)) == 1
