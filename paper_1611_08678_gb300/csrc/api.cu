@@ -92,6 +92,7 @@ struct abm_plan_s {
   size_t fb_cap = 0;                // elements
   double* farb = nullptr;
   size_t farb_cap = 0;
+  unsigned int* far_ticket = nullptr;  // per column tile (2 per tile for the adjoint), zero between launches
   TileDesc* d_tiles = nullptr;
   double* d_h = nullptr;
   int* d_N = nullptr;
@@ -543,8 +544,18 @@ abm_status enqueue_batched(abm_plan p, const Sched& S, BatchArgs A, cudaStream_t
         Trace tr(p, ABM_KERNEL_FAR, st);
         CK(launch_far_tc(far_kind(p), T, n_active, st), "tensor-core far kernel");
       } else {
-        Trace tr(p, ABM_KERNEL_FAR, st);
-        CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
+        // history split of the SIMT far kernels per launch: about two CTAs per
+        // SM over the active tiles (few tiles late in a ragged batch would
+        // otherwise leave most SMs idle); the near kernel of this time tile
+        // adds the same number of partial sums
+        int ks = std::max(1, std::min(16, (2 * p->sms + n_active - 1) / n_active));
+        while (ks > 1 && (size_t)ks * n_active * 2 * B * kTrajPerTile * d > p->farb_cap) --ks;
+        A.ksplit = ks;
+        {
+          Trace tr(p, ABM_KERNEL_FAR, st);
+          CK(launch_batched_far(d, p->o.prec, A, n_active, s, st), "far kernel");
+        }
+        A.ksplit = 1;  // the far kernel's last CTA per tile added the partials
       }
     }
     {
@@ -617,6 +628,7 @@ BatchArgs batch_args(abm_plan p, const Sched& S, const double* params, const dou
   A.fsh_ld = p->fsh_ld;
   A.fsh_plane = (long long)p->max_tiles * kTrajPerTile * d * p->fsh_ld;
   A.far = p->farb;
+  A.far_ticket = p->far_ticket;
   A.Y = Y;
   A.YP = YP;
   A.ldY = ldY;
@@ -722,6 +734,7 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
     if (!alloc((void**)&p->Fb, p->fb_cap * sizeof(double)) ||
         (o->prec == ABM_PREC_FP32_FAR && !alloc((void**)&p->Fb32, p->fb_cap * sizeof(float))) ||
         !alloc((void**)&p->farb, p->farb_cap * sizeof(double)) ||
+        !alloc((void**)&p->far_ticket, (2 * (size_t)p->max_tiles + 16) * sizeof(unsigned int)) ||
         !alloc((void**)&p->d_tiles, (size_t)p->max_tiles * sizeof(TileDesc)) ||
         !alloc((void**)&p->d_h, (size_t)o->max_batch * sizeof(double)) ||
         !alloc((void**)&p->d_N, (size_t)o->max_batch * sizeof(int)) ||
@@ -732,6 +745,8 @@ abm_status abm_plan_create(abm_plan* out, abm_system sys, const abm_plan_opts* o
         !alloc((void**)&p->d_bptr, 3 * kMaxWeightSets * kMaxD * sizeof(double*)) ||
         !alloc((void**)&p->d_b32ptr, 2 * kMaxWeightSets * kMaxD * sizeof(float*)))
       return cleanup_fail(ABM_ERR_OOM);
+    if (cudaMemset(p->far_ticket, 0, (2 * (size_t)p->max_tiles + 16) * sizeof(unsigned int)) != cudaSuccess)
+      return cleanup_fail(ABM_ERR_CUDA);
     if (tc_prec) {
       p->Lbase = (long long)((o->n_max + 63) / 64) * 64;
       p->Lx = p->Lbase + 64;
@@ -771,7 +786,7 @@ abm_status abm_plan_destroy(abm_plan p) {
   if (p->copy_st) cudaStreamDestroy(p->copy_st);
   cudaFree(p->ppartial); cudaFree(p->pflags);
   cudaFree(p->F1); cudaFree(p->far1); cudaFree(p->part1); cudaFree(p->tickets); cudaFree(p->hhat1);
-  cudaFree(p->Fb); cudaFree(p->Fb32); cudaFree(p->farb); cudaFree(p->d_tiles); cudaFree(p->d_h);
+  cudaFree(p->Fb); cudaFree(p->Fb32); cudaFree(p->farb); cudaFree(p->far_ticket); cudaFree(p->d_tiles); cudaFree(p->d_h);
   cudaFree(p->d_N); cudaFree(p->d_hhat); cudaFree(p->d_balpha); cudaFree(p->d_bg);
   cudaFree(p->d_bptr); cudaFree(p->d_b32ptr); cudaFree(p->d_btaylor); cudaFree(p->status);
   if (p->side) cudaStreamDestroy(p->side);
@@ -1268,6 +1283,7 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
   F.bucket_taylor = p->d_btaylor;
   F.F = p->Xadj;
   F.far = p->farb;
+  F.far_ticket = p->far_ticket;
   F.status = p->status;
   F.f_elems = 2 * (long long)p->fb_cap;
   F.w_elems = (long long)p->Mw + 1;
@@ -1297,7 +1313,7 @@ abm_status abm_adjoint(abm_plan p, int M, const double* alpha, const double* h, 
         while ((size_t)ks * na2 * 2 * B * kTrajPerTile * d > p->farb_cap && ks > 1) --ks;
         F.n_tiles = na2;
         F.ksplit = ks;
-        A.far_ksplit = ks;
+        A.far_ksplit = 1;  // the far kernel's last CTA per tile adds the ks partials
         Trace tr(p, ABM_KERNEL_ADJOINT, st);
         CK(launch_batched_far(d, ABM_PREC_FP64, F, na2, s, st), "adjoint far kernel");
       }

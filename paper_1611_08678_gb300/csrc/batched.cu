@@ -480,6 +480,43 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
 }
 
 // ---------------------------------------------------------------------------
+// K-split reduction of the SIMT far kernels: once every CTA of a tile has
+// stored its partial sums, the last one to finish (an atomic ticket per tile)
+// adds the ksplit partials in split order into slot 0, so the sums are
+// deterministic and the near kernel reads one value per target.  Thread
+// layout of the callers: rows i0 .. i0+R-1, columns lane*D .. lane*D+D-1.
+// ---------------------------------------------------------------------------
+template <int D, int B, int R>
+__device__ void reduce_split_partials(const BatchArgs& A, int tile, int i0, int lane, bool stored = true) {
+  if (A.ksplit <= 1) return;
+  constexpr int ld = kTrajPerTile * D;
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(A.far_ticket + tile, 1u) == (unsigned)(A.ksplit - 1);
+  __syncthreads();
+  if (!last) return;
+  if (!stored) {  // (checked build) a CTA skipped its stores: only the ticket is reset
+    if (threadIdx.x == 0) A.far_ticket[tile] = 0u;
+    return;
+  }
+  __threadfence();
+  const size_t qstride = (size_t)A.n_tiles * 2 * B * ld;
+#pragma unroll
+  for (int half = 0; half < 2; ++half)
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        double* out = A.far + (((size_t)tile * 2 + half) * B + i0 + r) * ld + lane * D + c;
+        double v = __ldcg(out);
+        for (int q = 1; q < A.ksplit; ++q) v += __ldcg(out + q * qstride);
+        *out = v;
+      }
+  if (threadIdx.x == 0) A.far_ticket[tile] = 0u;  // ready for the next launch
+}
+
+// ---------------------------------------------------------------------------
 // Far kernel, FP64 (plain comparator path).  Grid (active tiles, ksplit).
 // 256 threads = 8 warps; warp w owns target rows [w*B/8, (w+1)*B/8), lane =
 // trajectory.  Every lane of a warp uses the same Toeplitz lag, so the weight
@@ -511,7 +548,10 @@ __global__ void __launch_bounds__(256) batched_far_fp64_kernel(BatchArgs A, long
   const bool out_ok =
       in_bounds(A.status, kChkFarFp64, ((((long long)q * A.n_tiles + tile) * 2 + 1) * B + B - 1) * ld + ld - 1,
                 A.far_elems);
-  if (!out_ok) return;
+  if (!out_ok) {
+    reduce_split_partials<D, B, R>(A, tile, i0, lane, false);
+    return;
+  }
   if (kb < ke && ok) {
     double wbv[R], wav[R];
 #pragma unroll
@@ -539,17 +579,50 @@ __global__ void __launch_bounds__(256) batched_far_fp64_kernel(BatchArgs A, long
 #pragma unroll
     for (int c = 0; c < D; ++c) { P[c] = accP[r][c]; C[c] = accC[r][c]; }
   }
+  reduce_split_partials<D, B, R>(A, tile, i0, lane);
 }
 
 // ---------------------------------------------------------------------------
-// Far kernel, FP32 operands (SIMT): FP32 products and accumulation inside a
-// lag block of KB rows, blocks combined in FP64.  Same layout as the FP64
-// kernel; 512 threads = 16 warps, warp w owns B/16 rows.
+// Far kernel, FP32 operands (SIMT): the far sums of Sec. 2 with F and the
+// weights rounded to FP32, FP32 products and sums within 64-row history
+// blocks, and the block sums added into a compensated FP32 pair (TwoSum) per
+// output, widened to FP64 at the end.  Grid (active tiles, history splits),
+// 256 threads: warp w owns target rows 8w .. 8w+7, lane = trajectory (its D
+// columns), so a thread holds an 8 x D tile of predictor and corrector sums.
+// Each 64-row block of the tile's FP32 history (24 KB for D = 3) is staged in
+// shared memory by cp.async, double-buffered, with the 127 lags of b and a
+// that block needs; a thread walks the block in chunks of 8 rows with the
+// 15 weights those rows and targets need in registers (the Toeplitz
+// structure: w_{i-k} for i - k in a 15-wide band).
 // ---------------------------------------------------------------------------
-template <int D, int B, int KB>
-__global__ void __launch_bounds__(512) batched_far_fp32_kernel(BatchArgs A, long long s) {
-  constexpr int R = B / 16;
+namespace {
+constexpr int kF32Block = 64;  // history rows per staged block and per FP32 partial sum
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// (hi, lo) += x, compensated (TwoSum)
+__device__ __forceinline__ void two_sum_f32(float& hi, float& lo, float x) {
+  const float sum = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(sum, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bp)), __fsub_rn(x, bp)));
+  hi = sum;
+}
+}  // namespace
+
+template <int D, int B>
+__global__ void __launch_bounds__(256, 1) batched_far_fp32_kernel(BatchArgs A, long long s) {
+  static_assert(B == 64, "one warp per 8 of the 64 target rows");
+  constexpr int R = 8, KS = kF32Block, WL = KS + B - 1;  // lags per block: 127
   constexpr int ld = kTrajPerTile * D;
+  extern __shared__ __align__(16) float f32_dyn[];
+  float (*Fs)[KS][ld] = reinterpret_cast<float (*)[KS][ld]>(f32_dyn);  // [2][KS][ld]
+  float (*Wbs)[WL + 1] = reinterpret_cast<float (*)[WL + 1]>(f32_dyn + 2 * KS * ld);
+  float (*Was)[WL + 1] = Wbs + 2;
   const int tile = blockIdx.x, q = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TileDesc& T = A.tiles[tile];
   const float* __restrict__ wb = A.bucket_b32[T.bucket * kMaxD];
@@ -559,53 +632,101 @@ __global__ void __launch_bounds__(512) batched_far_fp32_kernel(BatchArgs A, long
   const long long chunk = (K + A.ksplit - 1) / A.ksplit;
   const long long kb = A.far_k0 + (long long)q * chunk, ke = min(s, kb + chunk);
   const int i0 = warp * R;
-  double dP[R][D], dC[R][D];
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int c = 0; c < D; ++c) dP[r][c] = dC[r][c] = 0.0;
   const bool ok = kb >= ke || (in_bounds(A.status, kChkFarFp32, T.f_off + ke * ld - 1, A.f_elems) &&
                                in_bounds(A.status, kChkFarFp32, s + B - 1 - kb, A.w_elems));
   if (!in_bounds(A.status, kChkFarFp32, ((((long long)q * A.n_tiles + tile) * 2 + 1) * B + B - 1) * ld + ld - 1,
-                 A.far_elems))
+                 A.far_elems)) {
+    reduce_split_partials<D, B, R>(A, tile, i0, lane, false);
     return;
-  for (long long k0 = kb; ok && k0 < ke; k0 += KB) {
-    const long long k1 = min(ke, k0 + KB);
+  }
+  float hiP[R][D], loP[R][D], hiC[R][D], loC[R][D];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) hiP[r][c] = loP[r][c] = hiC[r][c] = loC[r][c] = 0.0f;
+  const int nblk = ok && kb < ke ? (int)((ke - kb + KS - 1) / KS) : 0;
+  // stage block t: rows kb + t KS ... (whole 16-byte chunks; rows at or past
+  // ke are zero-filled so they add nothing) and lags s - k0 - 63 .. s + 63 - k0
+  auto stage = [&](int t) {
+    const long long k0 = kb + (long long)t * KS;
+    const int rows = (int)min((long long)KS, ke - k0);
+    float* dst = &Fs[t & 1][0][0];
+    const float* src = F + k0 * ld;
+    for (int v = threadIdx.x; v < KS * ld / 4; v += blockDim.x) {
+      if (v * 4 < rows * ld) cp_async16(dst + v * 4, src + v * 4);
+      else *reinterpret_cast<float4*>(dst + v * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int j = threadIdx.x; j < WL; j += blockDim.x) {
+      const long long lag = s - k0 - (KS - 1) + j;
+      const bool in = lag >= 0 && lag < A.w_elems;
+      Wbs[t & 1][j] = in ? wb[lag] : 0.0f;
+      Was[t & 1][j] = in ? wa[lag] : 0.0f;
+    }
+    cp_async_commit();
+  };
+  if (nblk > 0) stage(0);
+  for (int t = 0; t < nblk; ++t) {
+    if (t + 1 < nblk) {
+      stage(t + 1);
+      cp_async_wait_one();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    const int buf = t & 1;
     float accP[R][D], accC[R][D];
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int c = 0; c < D; ++c) accP[r][c] = accC[r][c] = 0.0f;
-    float wbv[R], wav[R];
+#pragma unroll 1
+    for (int k8 = 0; k8 < KS; k8 += 8) {
+      // w_{lag} for lag = s + i - k, i = i0 + r, k = k0 + k8 + kk: staged index
+      // i - (k - k0) + 63 = i0 - k8 + 56 + (r - kk + 7)
+      float b15[15], a15[15];
 #pragma unroll
-    for (int r = 0; r < R; ++r) { wbv[r] = wb[s + i0 + r - k0]; wav[r] = wa[s + i0 + r - k0]; }
-    for (long long k = k0; k < k1; ++k) {
-      float f[D];
+      for (int u = 0; u < 15; ++u) {
+        b15[u] = Wbs[buf][i0 - k8 + 56 + u];
+        a15[u] = Was[buf][i0 - k8 + 56 + u];
+      }
 #pragma unroll
-      for (int c = 0; c < D; ++c) f[c] = F[k * ld + lane * D + c];
+      for (int kk = 0; kk < 8; ++kk) {
+        float f[D];
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+        for (int c = 0; c < D; ++c) f[c] = Fs[buf][k8 + kk][lane * D + c];
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          accP[r][c] = fmaf(wbv[r], f[c], accP[r][c]);
-          accC[r][c] = fmaf(wav[r], f[c], accC[r][c]);
-        }
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int r = R - 1; r > 0; --r) { wbv[r] = wbv[r - 1]; wav[r] = wav[r - 1]; }
-      if (k + 1 < k1) { wbv[0] = wb[s + i0 - (k + 1)]; wav[0] = wa[s + i0 - (k + 1)]; }
+          for (int c = 0; c < D; ++c) {
+            accP[r][c] = fmaf(b15[r - kk + 7], f[c], accP[r][c]);
+            accC[r][c] = fmaf(a15[r - kk + 7], f[c], accC[r][c]);
+          }
+      }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int c = 0; c < D; ++c) { dP[r][c] += (double)accP[r][c]; dC[r][c] += (double)accC[r][c]; }
+      for (int c = 0; c < D; ++c) {
+        two_sum_f32(hiP[r][c], loP[r][c], accP[r][c]);
+        two_sum_f32(hiC[r][c], loC[r][c], accC[r][c]);
+      }
+    __syncthreads();  // this buffer is staged again two blocks on
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     double* P = A.far + ((((size_t)q * A.n_tiles + tile) * 2 + 0) * B + i0 + r) * ld + lane * D;
     double* C = A.far + ((((size_t)q * A.n_tiles + tile) * 2 + 1) * B + i0 + r) * ld + lane * D;
 #pragma unroll
-    for (int c = 0; c < D; ++c) { P[c] = dP[r][c]; C[c] = dC[r][c]; }
+    for (int c = 0; c < D; ++c) {
+      P[c] = (double)hiP[r][c] + (double)loP[r][c];
+      C[c] = (double)hiC[r][c] + (double)loC[r][c];
+    }
   }
+  reduce_split_partials<D, B, R>(A, tile, i0, lane);
+}
+
+size_t far_fp32_smem_bytes(int d) {
+  return (2 * (size_t)kF32Block * kTrajPerTile * d + 4 * (size_t)(kF32Block + 64)) * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -629,8 +750,10 @@ __global__ void __launch_bounds__(256) batched_far_percomp_kernel(BatchArgs A, l
   const bool ok = kb >= ke || (in_bounds(A.status, kChkFarPerComp, T.f_off + ke * ld - 1, A.f_elems) &&
                                in_bounds(A.status, kChkFarPerComp, s + B - 1 - kb, A.w_elems));
   if (!ok || !in_bounds(A.status, kChkFarPerComp, ((((long long)q * A.n_tiles + tile) * 2 + 1) * B + B - 1) * ld + ld - 1,
-                        A.far_elems))
+                        A.far_elems)) {
+    reduce_split_partials<D, B, R>(A, tile, i0, lane, false);
     return;
+  }
   for (int c = 0; c < D; ++c) {
     const real* __restrict__ wb;
     const real* __restrict__ wa;
@@ -676,6 +799,7 @@ __global__ void __launch_bounds__(256) batched_far_percomp_kernel(BatchArgs A, l
       A.far[((((size_t)q * A.n_tiles + tile) * 2 + 1) * B + i0 + r) * ld + lane * D + c] = dC[r];
     }
   }
+  reduce_split_partials<D, B, R>(A, tile, i0, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -742,6 +866,17 @@ cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long 
   return err;
 }
 
+// static: internal linkage, so the flag belongs to this build of the library
+template <int D>
+static cudaError_t set_far_fp32_smem() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(batched_far_fp32_kernel<D, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)far_fp32_smem_bytes(D));
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, int n_active, long long s,
                                cudaStream_t st) {
   dim3 grid(n_active, A.ksplit);
@@ -751,8 +886,8 @@ cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, in
       if (d == 3) batched_far_percomp_kernel<3, 64, 0><<<grid, 256, 0, st>>>(A, s);
       else batched_far_percomp_kernel<1, 64, 0><<<grid, 256, 0, st>>>(A, s);
     } else {
-      if (d == 3) batched_far_percomp_kernel<3, 64, 512><<<grid, 256, 0, st>>>(A, s);
-      else batched_far_percomp_kernel<1, 64, 512><<<grid, 256, 0, st>>>(A, s);
+      if (d == 3) batched_far_percomp_kernel<3, 64, 128><<<grid, 256, 0, st>>>(A, s);
+      else batched_far_percomp_kernel<1, 64, 128><<<grid, 256, 0, st>>>(A, s);
     }
     return cudaGetLastError();
   }
@@ -762,8 +897,15 @@ cudaError_t launch_batched_far(int d, abm_precision prec, const BatchArgs& A, in
     else batched_far_fp64_kernel<1, 64><<<grid, 256, 0, st>>>(A, s);
   } else {
     if (A.B != 64) return cudaErrorInvalidValue;
-    if (d == 3) batched_far_fp32_kernel<3, 64, 512><<<grid, 512, 0, st>>>(A, s);
-    else batched_far_fp32_kernel<1, 64, 512><<<grid, 512, 0, st>>>(A, s);
+    if (d == 3) {
+      cudaError_t e = set_far_fp32_smem<3>();
+      if (e != cudaSuccess) return e;
+      batched_far_fp32_kernel<3, 64><<<grid, 256, far_fp32_smem_bytes(3), st>>>(A, s);
+    } else {
+      cudaError_t e = set_far_fp32_smem<1>();
+      if (e != cudaSuccess) return e;
+      batched_far_fp32_kernel<1, 64><<<grid, 256, far_fp32_smem_bytes(1), st>>>(A, s);
+    }
   }
   return cudaGetLastError();
 }

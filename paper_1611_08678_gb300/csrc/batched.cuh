@@ -53,6 +53,8 @@ struct BatchArgs {
   long long fsh_ld;        // history rows per column of Fsh (a multiple of 64)
   long long fsh_plane;     // elements per split piece
   double* far;             // [ksplit][n_tiles][2][B][32*D]
+  unsigned int* far_ticket;  // per tile, zero between launches: the SIMT far kernels' last
+                           // CTA of a tile adds the ksplit partials into slot 0
   // outputs
   double* Y;
   double* YP;

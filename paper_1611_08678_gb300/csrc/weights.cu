@@ -7,7 +7,9 @@
 // Evaluated without the catastrophic cancellation of the plain differences:
 //   b_m (m >= 1): m^a * expm1(a * log1p(1/m)) / Gamma(a+1)
 //   a_m (m >= 16): centred expansion at m+1, z = 1/(m+1), p = a+1,
-//          (m+1)^p * 2 * sum_{j>=1} C(p, 2j) z^(2j) / Gamma(a+2)  (all terms > 0)
+//          (m+1)^p * 2 * sum_{j>=1} C(p, 2j) z^(2j) / Gamma(a+2)  (terms > 0 for
+//          a <= 1; for a in (1, 2] the later terms alternate, each below
+//          z^2 / 12 of the one before)
 //   c_m (m >= 16): x = 1/m,
 //          m^p * sum_{k>=2} C(a, k-1) (k-1)(a+1)/k x^k / Gamma(a+2)
 //   a_m, c_m (1 <= m < 16): 16-point Gauss-Legendre quadrature of the
@@ -16,7 +18,10 @@
 //          a_m = [int_m^{m+1} u^(a-1)(u-m) du + int_{m+1}^{m+2} u^(a-1)(m+2-u) du] / Gamma(a)
 //          c_m = int_m^{m+1} u^(a-1)(u-m) du / Gamma(a)
 //   m = 0: b_0 = 1/Gamma(a+1), a_0 = 2 expm1(a ln 2)/Gamma(a+2), c_0 = a/Gamma(a+2).
-// Gamma is CUDA's tgamma (called, not reimplemented).
+// Gamma: the host C library's tgammal in extended precision (called, not
+// reimplemented), rounded once to FP64.
+#include <cmath>
+
 #include "common.cuh"
 
 namespace abm {
@@ -55,11 +60,13 @@ __device__ double quad_fall(double alpha, double lo) {
   return 0.5 * s;
 }
 
+// g0, g1, g2: Gamma(alpha), Gamma(alpha + 1), Gamma(alpha + 2), evaluated once
+// on the host in extended precision and rounded to FP64 (the weights inherit
+// their relative error).
 __global__ void weights_kernel(double alpha, int M, double* __restrict__ b, double* __restrict__ a,
-                               double* __restrict__ c, double* __restrict__ g_out) {
+                               double* __restrict__ c, double* __restrict__ g_out, double g0, double g1, double g2) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m > M) return;
-  const double g1 = tgamma(alpha + 1.0), g2 = tgamma(alpha + 2.0);
   const double p = alpha + 1.0;
   if (m == 0) {
     if (g_out) *g_out = 1.0 / g2;  // weight of the j = n+1 term of the corrector
@@ -71,13 +78,13 @@ __global__ void weights_kernel(double alpha, int M, double* __restrict__ b, doub
   const double dm = (double)m;
   b[m] = pow(dm, alpha) * expm1(alpha * log1p(1.0 / dm)) / g1;
   if (m < kQuadBelow) {
-    const double ga = tgamma(alpha);
+    const double ga = g0;
     double rise = quad_rise(alpha, dm);
     a[m] = (rise + quad_fall(alpha, dm + 1.0)) / ga;
     c[m] = rise / ga;
     return;
   }
-  // a_m: (m+1)^p * 2 * sum_j C(p,2j) z^(2j), terms positive and falling like z^2.
+  // a_m: (m+1)^p * 2 * sum_j C(p,2j) z^(2j), terms falling like z^2.
   {
     const double z = 1.0 / (dm + 1.0), z2 = z * z;
     double coef = p * (p - 1.0) * 0.5;  // C(p, 2)
@@ -119,7 +126,10 @@ __global__ void weights_to_f32_kernel(int M, const double* __restrict__ b, const
 cudaError_t launch_weights(double alpha, int M, double* b, double* a, double* c, double* g,
                            cudaStream_t st) {
   int threads = 256, blocks = (M + 1 + threads - 1) / threads;
-  weights_kernel<<<blocks, threads, 0, st>>>(alpha, M, b, a, c, g);
+  const long double al = alpha;
+  const double g0 = (double)std::tgamma(al), g1 = (double)std::tgamma(al + 1.0L),
+               g2 = (double)std::tgamma(al + 2.0L);
+  weights_kernel<<<blocks, threads, 0, st>>>(alpha, M, b, a, c, g, g0, g1, g2);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,8 @@ def test_batched_fp32_far_error_reported(abm, system, alphas):
     errs = _errors(batch, Y, t_max=5.0)
     print(f"{system} fp32 max rel err (t<=5): {errs.max():.3e}")
     assert errs.max() <= 1e-6
+    for i in range(batch.M):  # rows beyond N_i untouched
+        assert np.all(Y[i, int(batch.N[i]) + 1:] == 0.0)
 
 
 def test_batched_single_equivalence(abm):
@@ -295,9 +297,12 @@ def test_batched_near_split(abm, near_split, prec, system):
             worst = max(worst, float(np.abs(Y[i, : N + 1] - Yo).max() / np.abs(Yo).max()))
     else:
         worst = float(_errors(batch, Y, t_max=5.0).max())
-    # FP32 far sums (512-row FP32 blocks) reach 1.7e-6 on this batch with the
-    # one-CTA kernel as well: the split changes only the FP64 window order
-    tol = {"fp64": 1e-11, "bf16x6": 1e-6, "fp32": 5e-6}[prec]
+    # FP32 far sums (FP32 within 64-row blocks, a compensated FP32 sum across):
+    # on this batch the error, 1.70e-6, is set by rounding F and the weights to
+    # FP32, not by the sums (512-row FP32 blocks gave the same value), so the
+    # literal FP32 path is held to 2e-6 here; it stays within 1e-6 on the
+    # other batches and on the full Roessler workload (test_gpu_full_size)
+    tol = {"fp64": 1e-11, "bf16x6": 1e-6, "fp32": 2e-6}[prec]
     assert worst <= tol, (near_split, prec, system, worst)
 
 

@@ -22,8 +22,10 @@ def abm():
 
 
 # FP64 weights from the stable series / quadrature against the oracle's
-# binary128 values rounded to FP64.  Budget: tgamma (CUDA documents a few ulp),
-# pow (<= 2 ulp) and a short positive sum: 32 ulp.
+# binary128 values rounded to FP64.  Gamma comes from the host in extended
+# precision; pow (<= 2 ulp), the series and the 16-point quadrature leave
+# measured maxima of 5 ulp (b) and 17 ulp (a, c, at alpha = 0.05) on a
+# GB300: the bound is 20 ulp.
 @pytest.mark.parametrize("alpha", [0.05, 0.3, 0.5, 0.85, 0.9, 0.95, 0.98, 1.0])
 def test_weights_match_oracle(abm, alpha):
     M = 1 << 18
@@ -31,10 +33,14 @@ def test_weights_match_oracle(abm, alpha):
     b, a, c = (t.cpu().numpy() for t in plan.weights(alpha, M))
     plan.sync()
     ob, oa, oc, _ = oracle.weights(alpha, M)
-    for got, ref in ((b, ob), (a, oa), (c, oc)):
+    worst = {}
+    for name, got, ref in (("b", b, ob), ("a", a, oa), ("c", c, oc)):
         ulp = np.spacing(np.abs(ref))
         err_ulp = np.abs(got - ref) / ulp
-        assert np.max(err_ulp) <= 32, (alpha, int(np.argmax(err_ulp)), float(np.max(err_ulp)))
+        worst[name] = float(np.max(err_ulp))
+        assert np.max(err_ulp) <= (8 if name == "b" else 20), (alpha, name, int(np.argmax(err_ulp)),
+                                                               float(np.max(err_ulp)))
+    print(f"weights alpha={alpha}: max ulp b {worst['b']:.1f}, a {worst['a']:.1f}, c {worst['c']:.1f}")
 
 
 def test_weights_alpha_one_exact_values(abm):
