@@ -80,7 +80,7 @@ __global__ void batched_setup_kernel(BatchArgs A) {
 // helpers, each chain warp sums its whole window itself (fewer instructions;
 // best when several tiles share an SM and hide each other's latency).
 // ---------------------------------------------------------------------------
-template <int SYS, int HS>
+template <int SYS, int HS, int NC>
 __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kernel(BatchArgs A, long long s, int nb) {
   using S = Sys<SYS>;
   constexpr int D = S::D;
@@ -94,8 +94,11 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
   double (*Rp)[HSX][ld] = reinterpret_cast<double (*)[HSX][ld]>(near_dyn + 65 * ld);
   double (*Rc)[HSX][ld] = reinterpret_cast<double (*)[HSX][ld]>(near_dyn + (65 + 2 * HS) * ld);
   __shared__ double ysh[2][D][32], ysh2[2][D][32];  // predictor / corrector exchange
-  // per component: lags 0..64 of its weights, b_n and c_n of this tile's targets
-  __shared__ double wsb_[D][65], wsa_[D][65], bns_[D][64], cns_[D][64];
+  // per weight set (NC = 1: every component; NC = D: one per component, for
+  // orders that differ per component): lags 0..64, b_n and c_n of this tile's
+  // targets.  NC is a template parameter so that equal orders keep the small
+  // static footprint (four CTAs of the chain-only kernel per SM).
+  __shared__ double wsb_[NC][65], wsa_[NC][65], bns_[NC][64], cns_[NC][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool chain = warp < D;
   const int c = chain ? warp : (warp - D) % D;  // component (column group)
@@ -108,19 +111,20 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
   const double alpha = A.bucket_alpha[bk];  // the system's own use of alpha
   const int col = lane * D + c;  // this thread's history column
   double* __restrict__ F = A.F + T.f_off;
-  for (int m = threadIdx.x; m < D * 65; m += NT) {
+  for (int m = threadIdx.x; m < NC * 65; m += NT) {
     wsb_[m / 65][m % 65] = A.bucket_b[bk + m / 65][m % 65];
     wsa_[m / 65][m % 65] = A.bucket_a[bk + m / 65][m % 65];
   }
   const bool w_ok = in_bounds(A.status, kChkNear, s + 63, A.w_elems);
-  for (int m = threadIdx.x; m < D * 64; m += NT) {
+  for (int m = threadIdx.x; m < NC * 64; m += NT) {
     bns_[m / 64][m % 64] = w_ok ? A.bucket_b[bk + m / 64][s + m % 64] : 0.0;
     cns_[m / 64][m % 64] = w_ok ? A.bucket_c[bk + m / 64][s + m % 64] : 0.0;
   }
-  const double* wsb = wsb_[c];  // this warp's component
-  const double* wsa = wsa_[c];
-  const double* bns = bns_[c];
-  const double* cns = cns_[c];
+  const int wset = NC == 1 ? 0 : c;  // this warp's component's weight set
+  const double* wsb = wsb_[wset];
+  const double* wsa = wsa_[wset];
+  const double* bns = bns_[wset];
+  const double* cns = cns_[wset];
   // the tile's rows s .. s + nb are read or written below
   const bool f_ok = in_bounds(A.status, kChkNear, T.f_off + (s + nb + 1) * ld - 1, A.f_elems);
   for (int m = threadIdx.x; m < ld; m += NT) Fw[0][m] = f_ok ? F[s * ld + m] : 0.0;
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(32 * (HS + 1) * Sys<SYS>::D) batched_near_kern
 // (identical values), lane l = 0 stores.  Same inputs, outputs and history
 // layout as batched_near_kernel (the parts of a tile write disjoint columns).
 // ---------------------------------------------------------------------------
-template <int SYS, int L>
+template <int SYS, int L, int NC>
 __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(BatchArgs A, long long s, int nb) {
   using S = Sys<SYS>;
   constexpr int D = S::D;
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
   constexpr int ldc = T * D;                // columns of this CTA
   __shared__ double Fw[65][ldc];            // f rows s..s+64 of this CTA's columns
   __shared__ double ysh[2][D][T], ysh2[2][D][T];
-  __shared__ double wsb_[D][65], wsa_[D][65], bns_[D][64], cns_[D][64];  // per component
+  __shared__ double wsb_[NC][65], wsa_[NC][65], bns_[NC][64], cns_[NC][64];  // per weight set
   const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;  // component, lane
   const int j = lane / L, l = lane % L;                      // trajectory of the part, lag slice
   const int tile = blockIdx.x / L, part = blockIdx.x % L;
@@ -330,19 +334,20 @@ __global__ void __launch_bounds__(32 * Sys<SYS>::D) batched_near_split_kernel(Ba
   const int cloc = j * D + c;                // column in this CTA's window
   double* __restrict__ F = A.F + Td.f_off;
   constexpr int NT = 32 * D;
-  for (int m = threadIdx.x; m < D * 65; m += NT) {
+  for (int m = threadIdx.x; m < NC * 65; m += NT) {
     wsb_[m / 65][m % 65] = A.bucket_b[bk + m / 65][m % 65];
     wsa_[m / 65][m % 65] = A.bucket_a[bk + m / 65][m % 65];
   }
   const bool w_ok = in_bounds(A.status, kChkNearSplit, s + 63, A.w_elems);
-  for (int m = threadIdx.x; m < D * 64; m += NT) {
+  for (int m = threadIdx.x; m < NC * 64; m += NT) {
     bns_[m / 64][m % 64] = w_ok ? A.bucket_b[bk + m / 64][s + m % 64] : 0.0;
     cns_[m / 64][m % 64] = w_ok ? A.bucket_c[bk + m / 64][s + m % 64] : 0.0;
   }
-  const double* wsb = wsb_[c];  // this warp's component
-  const double* wsa = wsa_[c];
-  const double* bns = bns_[c];
-  const double* cns = cns_[c];
+  const int wset = NC == 1 ? 0 : c;  // this warp's component's weight set
+  const double* wsb = wsb_[wset];
+  const double* wsa = wsa_[wset];
+  const double* bns = bns_[wset];
+  const double* cns = cns_[wset];
   const bool f_ok = in_bounds(A.status, kChkNearSplit, Td.f_off + (s + nb + 1) * ldt - 1, A.f_elems);
   for (int m = threadIdx.x; m < ldc; m += NT) Fw[0][m] = f_ok ? F[s * ldt + part * ldc + m] : 0.0;
   const int kfirst = s > 1 ? 0 : 1;  // window rows relative to s (row 0 is f_0 when s = 0)
@@ -811,29 +816,38 @@ cudaError_t launch_batched_setup(int sys, const BatchArgs& A, int n_tiles, cudaS
 // static: internal linkage, so the flag below belongs to this build of the
 // library (a function-local static of an external template is one object for
 // the whole process, shared by every loaded build)
-template <int SYS, int HS>
-static cudaError_t launch_near_t(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+template <int SYS, int HS, int NC>
+static cudaError_t launch_near_nc(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
   constexpr int D = Sys<SYS>::D;
   const size_t smem = (size_t)(65 + 4 * HS) * kTrajPerTile * D * sizeof(double);
   static bool attr_set = false;  // per instantiation; a plan is used from one thread
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(batched_near_kernel<SYS, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(batched_near_kernel<SYS, HS, NC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // the far kernels between these launches need the largest shared-memory
     // carveout; asking for it here too saves a reconfiguration per switch
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(batched_near_kernel<SYS, HS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+      e = cudaFuncSetAttribute(batched_near_kernel<SYS, HS, NC>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  batched_near_kernel<SYS, HS><<<n_active, 32 * (HS + 1) * D, smem, st>>>(A, s, nb);
+  batched_near_kernel<SYS, HS, NC><<<n_active, 32 * (HS + 1) * D, smem, st>>>(A, s, nb);
   return cudaGetLastError();
+}
+
+template <int SYS, int HS>
+static cudaError_t launch_near_t(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
+  if (A.per_comp) return launch_near_nc<SYS, HS, Sys<SYS>::D>(A, n_active, s, nb, st);
+  return launch_near_nc<SYS, HS, 1>(A, n_active, s, nb, st);
 }
 
 template <int SYS, int L>
 cudaError_t launch_near_split_t(const BatchArgs& A, int n_active, long long s, int nb, cudaStream_t st) {
-  batched_near_split_kernel<SYS, L><<<n_active * L, 32 * Sys<SYS>::D, 0, st>>>(A, s, nb);
+  if (A.per_comp)
+    batched_near_split_kernel<SYS, L, Sys<SYS>::D><<<n_active * L, 32 * Sys<SYS>::D, 0, st>>>(A, s, nb);
+  else
+    batched_near_split_kernel<SYS, L, 1><<<n_active * L, 32 * Sys<SYS>::D, 0, st>>>(A, s, nb);
   return cudaGetLastError();
 }
 
