@@ -232,14 +232,17 @@ __global__ void __launch_bounds__(THREADS, 1) far_tc_kernel(FarTcArgs A) {
             break;
           }
           tc::fence_after_sync();
-          const uint32_t sa = tc::smem_u32(smem + ws * W_STAGE);
-          const uint32_t sbb = tc::smem_u32(smem_f + fs * F_STAGE);
+          // descriptors of the two stage bases; every operand is base + a constant
+          // offset, added to the 14-bit start-address field (the shared window is
+          // below 256 KB, so it cannot carry into the next field)
+          const uint64_t ad0 = tc::sdesc_kmajor_sw128(tc::smem_u32(smem + ws * W_STAGE));
+          const uint64_t bd0 = tc::sdesc_kmajor_sw128(tc::smem_u32(smem_f + fs * F_STAGE));
 #pragma unroll
           for (int kk = 0; kk < KB / 16; ++kk) {
 #pragma unroll
             for (int pr = 0; pr < NPROD; ++pr) {
-              const uint64_t ad = tc::sdesc_kmajor_sw128(sa + PA[pr] * A_BYTES + kk * 32);
-              const uint64_t bd = tc::sdesc_kmajor_sw128(sbb + PB[pr] * B_BYTES + kk * 32);
+              const uint64_t ad = ad0 + (uint64_t)((PA[pr] * A_BYTES + kk * 32) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((PB[pr] * B_BYTES + kk * 32) >> 4);
               if (pr == 0) {
                 tc::mma_bf16(d_main, ad, bd, idesc, first_main ? 0u : 1u);
                 first_main = false;
