@@ -94,7 +94,7 @@ def parse_args(argv=None):
                     help="batched: corrector passes per step (1 = PECE, m > 1 = P(EC)^m E)")
     ap.add_argument("--trajectories", type=int, default=0,
                     help="batched workloads: first M trajectories only (small cases for profiling)")
-    ap.add_argument("--arms", default="bf16x3",
+    ap.add_argument("--arms", default="bf16x3,fp32",
                     help="batched: further far-history precisions run on the full workload beside the "
                          "headline one (comma list of bf16x3, bf16x6, fp32, fp64; empty for none)")
     ap.add_argument("--no-comparator", action="store_true",
@@ -284,25 +284,26 @@ def bench_single(args, name, w, world, rank, local):
     mean_launch = total / args.steps
     achieved = 2.0 * macs / mean_launch / 1e12
 
-    # e2e: the public call with host buffers: params / y0 from pinned host
-    # memory (by value through the ABI), the solution copied back to pinned
-    # host memory, every step.
+    # e2e: one C-ABI call with host buffers (abm_solve_host): params / y0 from
+    # host memory (passed by value), the solution written to pinned host
+    # memory, every step.
     Yh = torch.empty(N + 1, d, dtype=torch.float64, pin_memory=True)
-    p_host = torch.tensor(w.params[0], dtype=torch.float64).pin_memory()
-    y0_host = torch.tensor(w.y0[0], dtype=torch.float64).pin_memory()
+    p_host = np.ascontiguousarray(w.params[0], dtype=np.float64)
+    y0_host = np.ascontiguousarray(w.y0[0], dtype=np.float64)
     e2e_steps = max(2, args.steps // 2)
+    plan.solve_host(alpha, h, N, p_host, y0_host, Y=Yh, stream=stream)  # allocates the plan's device copy
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        plan.solve(alpha, h, N, p_host.numpy(), y0_host.numpy(), Y=Y, sync=False, stream=stream)
-        Yh.copy_(Y, non_blocking=True)
+        plan.solve_host(alpha, h, N, p_host, y0_host, Y=Yh, sync=False, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     plan.sync(stream)
     e2e_sec = e0.elapsed_time(e1) / 1e3
     e2e = {"value": e2e_steps * N * world / e2e_sec, "unit": "trajectory-steps/s",
-           "h2d_bytes_per_step": int((w.params.shape[1] + d) * 8), "d2h_bytes_per_step": int((N + 1) * d * 8)}
+           "h2d_bytes_per_step": int((w.params.shape[1] + d) * 8), "d2h_bytes_per_step": int((N + 1) * d * 8),
+           "entry_point": "abm_solve_host"}
 
     out = {
         "metric": "trajectory-steps/s (plain FP64 path; history MAC/s beside)",

@@ -203,6 +203,16 @@ abm_status abm_weights(abm_plan p, double alpha, int M, double* b, double* a, do
 abm_status abm_solve(abm_plan p, double alpha, double h, int N, const double* params,
                      const double* y0, double* Y, double* YP, void* stream);
 
+/* abm_solve with HOST buffers (the paper has no counterpart: it is the call a
+ * user makes with the result in host memory).  Arguments as abm_solve; Y (and
+ * YP when not NULL) are host arrays of (N+1)*d doubles, written once the
+ * solve has run (the solve writes into a device copy owned by the plan,
+ * allocated by the first call, then one copy per array is enqueued on
+ * `stream`).  The work is complete once `stream` has passed it
+ * (abm_plan_sync); page-locked host memory keeps the copies asynchronous. */
+abm_status abm_solve_host(abm_plan p, double alpha, double h, int N, const double* params, const double* y0,
+                          double* Y, double* YP, void* stream);
+
 /* The general problem of eq. (1) for one trajectory: an order per state
  * component, each in (0, 2] (a non-commensurate system when they differ), and
  * for components of order above one the initial derivative y_i'(0), which

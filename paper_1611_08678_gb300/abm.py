@@ -29,7 +29,7 @@ EXPORTS = ["abm_plan_opts_default", "abm_system_dim", "abm_system_nparams", "abm
            "abm_plan_destroy", "abm_plan_sync", "abm_last_error", "abm_weights", "abm_solve",
            "abm_solve_batched", "abm_solve_batched_host", "abm_adjoint", "abm_far_history", "abm_solve_noalloc",
            "abm_plan_kernel_times", "abm_solve_ext", "abm_solve_batched_ext", "abm_history", "abm_solve_resume",
-           "abm_history_batched", "abm_solve_batched_resume"]
+           "abm_history_batched", "abm_solve_batched_resume", "abm_solve_host"]
 KERNEL_KINDS = {"weights": 0, "far": 1, "near": 2, "single": 3, "adjoint": 4}
 
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         lib.abm_solve.argtypes = [_vp, D, D, I, _dp, _dp, _vp, _vp, _vp]
         lib.abm_solve_batched.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_solve_ext.argtypes = [_vp, _dp, D, I, _dp, _dp, _dp, _vp, _vp, _vp]
+        lib.abm_solve_host.argtypes = [_vp, D, D, I, _dp, _dp, _vp, _vp, _vp]
         lib.abm_solve_batched_ext.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_solve_batched_host.argtypes = [_vp, I, _dp, _dp, _ip, _vp, _vp, _vp, LL, _vp, _vp]
         lib.abm_history.argtypes = [_vp, I, _vp, _vp]
@@ -243,6 +244,30 @@ class Plan:
         st = self.lib.abm_solve(self.h, float(alpha), float(h), int(N), p.ctypes.data_as(_dp),
                                 y.ctypes.data_as(_dp), _dptr(Y), _dptr(YP), _stream_ptr(stream))
         self._check(st, "abm_solve")
+        if sync:
+            self.sync(stream)
+        return (Y, YP) if want_yp or YP is not None else Y
+
+    def solve_host(self, alpha, h, N, params, y0, Y=None, YP=None, want_yp=False, stream=None, sync=True):
+        """abm_solve_host: the single-trajectory solve with the result in host
+        memory (torch CPU tensors of shape (N+1, d), page-locked when
+        allocated here)."""
+        torch = _torch()
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        y = np.ascontiguousarray(y0, dtype=np.float64)
+        if p.size != self.np or y.size != self.d:
+            raise ValueError("params / y0 have the wrong size for this system")
+        if Y is None:
+            Y = torch.empty(N + 1, self.d, dtype=torch.float64, pin_memory=True)
+        if YP is None and want_yp:
+            YP = torch.empty(N + 1, self.d, dtype=torch.float64, pin_memory=True)
+        _check_out(Y, (N + 1, self.d), "Y", cuda=False, more_rows=True)
+        _check_out(YP, (N + 1, self.d), "YP", cuda=False, more_rows=True)
+        st = self.lib.abm_solve_host(self.h, float(alpha), float(h), int(N), p.ctypes.data_as(_dp),
+                                     y.ctypes.data_as(_dp), ctypes.c_void_p(Y.data_ptr()),
+                                     ctypes.c_void_p(YP.data_ptr()) if YP is not None else None,
+                                     _stream_ptr(stream))
+        self._check(st, "abm_solve_host")
         if sync:
             self.sync(stream)
         return (Y, YP) if want_yp or YP is not None else Y

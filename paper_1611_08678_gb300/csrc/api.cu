@@ -117,6 +117,7 @@ struct abm_plan_s {
   double *acc_dp = nullptr, *acc_dy0 = nullptr, *phi0c = nullptr;
   // host-buffer batched solve (abm_solve_batched_host; allocated by its first call)
   double *hio_params = nullptr, *hio_y0 = nullptr, *hio_Y = nullptr, *hio_YP = nullptr;
+  double *hio_Y1 = nullptr, *hio_YP1 = nullptr;  // abm_solve_host (single trajectory)
   cudaStream_t copy_st = nullptr;
   std::vector<cudaEvent_t> hio_ev;  // per time tile in which trajectories finish
   cudaEvent_t hio_done = nullptr;
@@ -781,6 +782,7 @@ abm_status abm_plan_destroy(abm_plan p) {
   cudaFree(p->acc_dp); cudaFree(p->acc_dy0); cudaFree(p->phi0c);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   cudaFree(p->hio_params); cudaFree(p->hio_y0); cudaFree(p->hio_Y); cudaFree(p->hio_YP);
+  cudaFree(p->hio_Y1); cudaFree(p->hio_YP1);
   for (cudaEvent_t e : p->hio_ev) cudaEventDestroy(e);
   if (p->hio_done) cudaEventDestroy(p->hio_done);
   if (p->copy_st) cudaStreamDestroy(p->copy_st);
@@ -960,6 +962,26 @@ abm_status abm_solve_ext(abm_plan p, const double* alpha, double h, int N, const
   for (int i = 0; i < p->d; ++i)
     if (!order_ok(alpha[i])) return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_ext: every order must be in (0, 2]");
   return solve_single(p, "abm_solve_ext", alpha, h, N, params, y0, y0d, Y, YP, (cudaStream_t)stream);
+}
+
+abm_status abm_solve_host(abm_plan p, double alpha, double h, int N, const double* params, const double* y0,
+                          double* Y, double* YP, void* stream) {
+  if (!p) return ABM_ERR_INVALID_ARG;
+  if (!alpha_ok(alpha) || !(std::isfinite(h) && h > 0.0) || N < 1 || N > p->o.n_max || !params || !y0 || !Y)
+    return fail(p, ABM_ERR_INVALID_ARG, "abm_solve_host: need alpha in (0,1], finite h > 0, 1 <= N <= n_max, "
+                                        "non-null params/y0/Y");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)(N + 1) * p->d * sizeof(double);
+  const size_t cap = (size_t)(p->o.n_max + 1) * p->d * sizeof(double);
+  if (!p->hio_Y1) CK(cudaMalloc(&p->hio_Y1, cap), "host-io Y");
+  if (YP && !p->hio_YP1) CK(cudaMalloc(&p->hio_YP1, cap), "host-io YP");
+  const double al[kMaxD] = {alpha, alpha, alpha};
+  abm_status rs = solve_single(p, "abm_solve_host", al, h, N, params, y0, nullptr, p->hio_Y1, YP ? p->hio_YP1 : nullptr,
+                               st);
+  if (rs) return rs;
+  CK(cudaMemcpyAsync(Y, p->hio_Y1, bytes, cudaMemcpyDeviceToHost, st), "copy-out");
+  if (YP) CK(cudaMemcpyAsync(YP, p->hio_YP1, bytes, cudaMemcpyDeviceToHost, st), "copy-out");
+  return ABM_OK;
 }
 
 abm_status abm_history(abm_plan p, int rows, double* F, void* stream) {

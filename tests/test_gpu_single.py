@@ -208,3 +208,15 @@ def test_single_wait_timeout_is_reported_not_hung(abm):
     Y = ok.solve(0.98, 0.01, 2000, p, y0).cpu().numpy()
     Yo, _ = oracle.solve("lorenz", 0.98, 0.01, 2000, p, y0)
     assert rel_err(Y[:501], Yo[:501]) <= 1e-11
+
+
+def test_single_host_buffers_match_device_call(abm):
+    """abm_solve_host: the same solve with the result in host memory."""
+    plan = abm.Plan("chen", n_max=3000)
+    p, y0 = [35.0, 3.0, 28.0], [-9.0, -5.0, 14.0]
+    Yd, YPd = plan.solve(0.9, 0.001, 3000, p, y0, want_yp=True)
+    Yh, YPh = plan.solve_host(0.9, 0.001, 3000, p, y0, want_yp=True)
+    assert np.array_equal(Yh.numpy(), Yd.cpu().numpy()) and np.array_equal(YPh.numpy()[1:], YPd.cpu().numpy()[1:])
+    Yp = torch.zeros(3001, 3, dtype=torch.float64)  # pageable
+    plan.solve_host(0.9, 0.001, 3000, p, y0, Y=Yp)
+    assert np.array_equal(Yp.numpy(), Yd.cpu().numpy())
