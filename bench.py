@@ -90,6 +90,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mib", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner (library defaults)")
+    ap.add_argument("--knobs", default="",
+                    help="batched: far_split,near_warps,near_split to use instead of tuning (e.g. the "
+                         "values a full-size run tuned, for a small profiling case)")
     ap.add_argument("--corrector-passes", type=int, default=1,
                     help="batched: corrector passes per step (1 = PECE, m > 1 = P(EC)^m E)")
     ap.add_argument("--trajectories", type=int, default=0,
@@ -540,7 +543,10 @@ def bench_batched(args, name, w, prec, world, rank, local):
     N = shard.N
     ldY = int(N.max()) + 1
     tuned = {"near_warps": 0, "far_split": 0, "near_split": 0}
-    if tc_far(prec) and not args.no_tune:
+    if args.knobs:
+        fs, nw, ns = (int(v) for v in args.knobs.split(","))
+        tuned = {"far_split": fs, "near_warps": nw, "near_split": ns, "cached": False, "results": []}
+    elif tc_far(prec) and not args.no_tune:
         from paper_1611_08678_gb300 import autotune
         tuned = autotune.tune_batched(shard, prec)  # untimed; cached per shape
     passes = args.corrector_passes
