@@ -68,11 +68,12 @@ NCU_TRAFFIC = {
 }
 # Batched far kernel: DRAM bytes of one captured launch over the algorithmic
 # operand bytes of that launch, per workload and precision (ncu captures of
-# 512-trajectory cases of the current kernel); the bench line scales it to its
-# own average launch, since DRAM bytes grow with the operand bytes.
+# the current kernel on a 512-trajectory Rossler and a 1024-trajectory
+# financial case, time tile 38464); the bench line scales it to its own
+# average launch, since DRAM bytes grow with the operand bytes.
 NCU_TRAFFIC_RATIO = {
-    "rossler_batched_bf16x6": (414428928 + 3322880) / 413564928,
-    "financial_batched_bf16x6": (385732352 + 3349248) / 384024576,
+    "rossler_batched_bf16x6": (414429952 + 3411456) / 413564928,
+    "financial_batched_bf16x6": (741771776 + 3026176) / 738508800,
 }
 
 
