@@ -122,12 +122,12 @@ typedef struct {
                           far_split times the waves (CTAs / SM count, rounded up)
                           of the unsplit launch; 0 = 2                           */
   int near_split;      /* batched near kernel: CTAs per column tile.  A tile's 32
-                          trajectories spread over 2, 4 or 8 CTAs (lanes of a
-                          trajectory sum interleaved slices of the lag window)
-                          so that few active tiles still use many SMs: 0 = the
-                          largest of 8 and 4 whose CTAs fit on the SMs, else
-                          none; 1 = never; 2, 4 or 8 = that split for every
-                          time tile                                          */
+                          trajectories spread over 2, 4, 8 or 16 CTAs (lanes
+                          of a trajectory sum interleaved slices of the lag
+                          window) so that few active tiles still use many SMs:
+                          0 = the largest of 8 and 4 whose CTAs fit on the
+                          SMs, else none; 1 = never; 2, 4, 8 or 16 = that
+                          split for every time tile (the adjoint runs 16 as 8) */
   int corrector_passes; /* corrector passes per step: 0 or 1 = PECE, the scheme
                           of Sec. 2; m = 2..8 = P(EC)^m E: the corrector, whose
                           last term g f(t_{n+1}, y_{n+1}) makes it implicit in

@@ -868,6 +868,10 @@ cudaError_t launch_batched_near(int sys, const BatchArgs& A, int n_active, long 
     ABM_DISPATCH_SYSTEM(sys, err = (launch_near_split_t<SYS, 8>(A, n_active, s, nb, st)));
     return err;
   }
+  if (split == 16) {
+    ABM_DISPATCH_SYSTEM(sys, err = (launch_near_split_t<SYS, 16>(A, n_active, s, nb, st)));
+    return err;
+  }
   if (wpc == 5) {
     ABM_DISPATCH_SYSTEM(sys, err = (launch_near_t<SYS, 4>(A, n_active, s, nb, st)));
   } else if (wpc == 3) {

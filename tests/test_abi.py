@@ -75,7 +75,7 @@ def test_plan_create_rejects_bad_options_before_any_cuda_call():
 
 @pytest.mark.parametrize("field,value,status", [
     ("prec", 4, 1), ("prec", -1, 1), ("near_warps", 4, 1), ("near_warps", 6, 1),
-    ("far_split", -1, 1), ("far_split", 65, 1), ("near_split", 3, 1), ("near_split", 16, 1),
+    ("far_split", -1, 1), ("far_split", 65, 1), ("near_split", 3, 1), ("near_split", 32, 1),
     ("far_ctas", -2, 1), ("spin_timeout_cycles", -5, 1), ("tile_B", -64, 1), ("tile_B", 128, 6),
     ("corrector_passes", -1, 1), ("corrector_passes", 9, 1),
 ])

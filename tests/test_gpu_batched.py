@@ -275,12 +275,12 @@ def test_batched_launch_shapes(abm, near_warps, prec, far_split):
     assert errs.max() <= tol, (near_warps, prec, far_split, errs.max())
 
 
-@pytest.mark.parametrize("near_split", [1, 2, 4, 8])
+@pytest.mark.parametrize("near_split", [1, 2, 4, 8, 16])
 @pytest.mark.parametrize("prec", ["fp64", "bf16x6", "fp32"])
 @pytest.mark.parametrize("system", ["rossler", "linear"])
 def test_batched_near_split(abm, near_split, prec, system):
-    """The split near kernel (each column tile's trajectories spread over 2, 4
-    or 8 CTAs, lanes of a trajectory summing interleaved lag slices) gives the
+    """The split near kernel (each column tile's trajectories spread over 2, 4,
+    8 or 16 CTAs, lanes of a trajectory summing interleaved lag slices) gives the
     oracle's trajectories like the one-CTA-per-tile kernel: FP64 within 1e-11,
     the reduced-precision far paths within their stated error.  Ragged N
     (tiles finishing mid-tile), several alpha groups, N not a multiple of 64."""
