@@ -744,7 +744,16 @@ def bench_adjoint(args, name, prec, world, rank, local):
     idx = shard_indices(w_all.M, rank, world, w_all.N) if world > 1 else np.arange(w_all.M)
     w, tparams = w_all.subset(idx), tparams_all[idx]
     N, M, d = int(w.N.max()), w.M, w.d
-    plan = abm.Plan("lorenz", n_max=N, max_batch=M, prec=prec, profile=True)
+    # launch shapes: pinned by --knobs, else tuned on the forward solve (the
+    # adjoint's far and near launches take the same plan options)
+    tuned = {"far_split": 0, "near_warps": 0, "near_split": 0}
+    if args.knobs:
+        tuned = dict(zip(("far_split", "near_warps", "near_split"), (int(v) for v in args.knobs.split(","))))
+    elif tc_far(prec) and not args.no_tune:
+        from paper_1611_08678_gb300 import autotune
+        tuned = autotune.tune_batched(w, prec)  # untimed; cached per shape
+    plan = abm.Plan("lorenz", n_max=N, max_batch=M, prec=prec, profile=True, far_split=tuned["far_split"],
+                    near_warps=tuned["near_warps"], near_split=tuned["near_split"])
     params = torch.as_tensor(w.params, device="cuda")
     y0 = torch.as_tensor(w.y0, device="cuda")
     Y = torch.zeros(M, N + 1, d, dtype=torch.float64, device="cuda")
@@ -796,6 +805,7 @@ def bench_adjoint(args, name, prec, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": f"f64 state, {prec} far", "data": "synthetic",
         "config": {"workload": name, "system": "lorenz", "trajectories": int(w_all.M), "N": N,
                    "far_precision": prec, "parallelism": f"trajectory shards x{world}",
+                   "tuned": {k: int(tuned[k]) for k in ("far_split", "near_warps", "near_split")},
                    "l2": "inputs larger than L2 (histories of 1024 trajectories, several GB)"},
         "history_mac_per_s": 2 * w_all.history_macs() * args.steps / total_max,
         "roofline": {"bound": "hbm", "achieved": byts / far_sec / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
